@@ -1,0 +1,191 @@
+"""Seeded synthetic transaction data shaped like the paper's pair-mining workloads.
+
+This module only produces inputs: vertical tidlists in CSR form and the three
+random permutations pi_1..pi_3 that the layout hash of Sec. III-A draws.  It
+holds none of the method's arithmetic and is shared by the CUDA path, the
+oracle, the tests and the benchmark.
+
+CSR convention (used everywhere in this repository):
+  offsets : uint64[n + 1], offsets[0] = 0, non-decreasing
+  tids    : uint32[offsets[n]], tids[offsets[i]:offsets[i+1]] is the tidlist
+            S_i of item i, strictly increasing, every value < m.
+Transaction ids are 0-based (the paper numbers them 1..m).
+
+Recipes (each a seeded numpy Generator, one independent stream per item):
+  * bernoulli: item i contains transaction x independently with probability p
+    (the instance generator of Sec. IV-A and the density sweep of Fig. 7).
+  * zipf: item of rank k (1..n) is included with probability
+    p_k = min(1, c / k**a); c is solved so that mean_k p_k equals the target
+    density, and ranks are shuffled onto item ids.  Transaction lengths are then
+    Poisson-binomial with mean density*n (close to Poisson for small p_k).
+  * pool: serving sets over a universe U with sizes drawn from a discrete
+    Zipf(1) law on [lo, hi]; members uniform (Bernoulli with p = size/U).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+__all__ = [
+    "Instance", "bernoulli_item", "bernoulli_tidlists", "zipf_probabilities",
+    "zipf_tidlists", "permutations", "config_instance", "batch_specs",
+    "pool_sizes", "pool_tidlists", "from_lists", "transactions_to_tidlists",
+    "CONFIGS",
+]
+
+
+@dataclass
+class Instance:
+    """One mining instance: m transactions, n items, tidlists in CSR form."""
+    m: int
+    n: int
+    offsets: np.ndarray  # uint64[n+1]
+    tids: np.ndarray     # uint32[T]
+    s: int = 0           # support threshold
+    name: str = ""
+
+    @property
+    def sizes(self) -> np.ndarray:
+        return np.diff(self.offsets).astype(np.int64)
+
+    def tidlist(self, i: int) -> np.ndarray:
+        return self.tids[int(self.offsets[i]):int(self.offsets[i + 1])]
+
+
+def _item_rng(seed: int, item: int) -> np.random.Generator:
+    return np.random.default_rng([int(seed), int(item)])
+
+
+def bernoulli_item(rng: np.random.Generator, m: int, p: float) -> np.ndarray:
+    """Sorted uint32 tids of one Bernoulli(p) subset of [0, m)."""
+    if m <= 0 or p <= 0.0:
+        return np.zeros(0, dtype=np.uint32)
+    if p >= 1.0:
+        return np.arange(m, dtype=np.uint32)
+    if p > 0.25:
+        return np.flatnonzero(rng.random(m) < p).astype(np.uint32)
+    # geometric gap sampling: O(|S|) work for sparse items
+    mean = m * p
+    out = []
+    pos = -1
+    while True:
+        cnt = int(mean + 6.0 * math.sqrt(mean) + 16)
+        gaps = rng.geometric(p, size=cnt).astype(np.int64)
+        pts = pos + np.cumsum(gaps)
+        if pts[-1] >= m:
+            out.append(pts[pts < m])
+            break
+        out.append(pts)
+        pos = int(pts[-1])
+    return np.concatenate(out).astype(np.uint32)
+
+
+def from_lists(lists, m: int, s: int = 0, name: str = "") -> Instance:
+    """Build an Instance from Python/numpy tidlists (sorted, unique, < m)."""
+    n = len(lists)
+    sizes = np.array([len(l) for l in lists], dtype=np.uint64)
+    offsets = np.zeros(n + 1, dtype=np.uint64)
+    np.cumsum(sizes, out=offsets[1:])
+    tids = (np.concatenate([np.asarray(l, dtype=np.uint32) for l in lists])
+            if n and int(offsets[-1]) else np.zeros(0, dtype=np.uint32))
+    return Instance(m=m, n=n, offsets=offsets, tids=tids.astype(np.uint32), s=s, name=name)
+
+
+def bernoulli_tidlists(m: int, n: int, p: float, seed: int, s: int = 0, name: str = "") -> Instance:
+    """Uniform density p for every item (configs 1 and 4)."""
+    return from_lists([bernoulli_item(_item_rng(seed, i), m, p) for i in range(n)], m, s, name)
+
+
+def zipf_probabilities(n: int, density: float, exponent: float = 1.0) -> np.ndarray:
+    """Per-rank inclusion probabilities p_k = min(1, c/k^a), mean = density."""
+    if n == 0:
+        return np.zeros(0)
+    k = np.arange(1, n + 1, dtype=np.float64)
+    base = k ** (-exponent)
+    target = density * n
+    lo, hi = 0.0, float(n) / base.min()
+    for _ in range(200):
+        c = 0.5 * (lo + hi)
+        if np.minimum(1.0, c * base).sum() < target:
+            lo = c
+        else:
+            hi = c
+    return np.minimum(1.0, 0.5 * (lo + hi) * base)
+
+
+def zipf_tidlists(m: int, n: int, density: float, seed: int, exponent: float = 1.0,
+                  s: int = 0, name: str = "") -> Instance:
+    """Zipf-skewed item frequencies with mean density `density` (configs 2, 3)."""
+    probs = zipf_probabilities(n, density, exponent)
+    rank_of_item = np.random.default_rng([int(seed), 0x5A1F]).permutation(n)
+    lists = [bernoulli_item(_item_rng(seed, i), m, float(probs[rank_of_item[i]]))
+             for i in range(n)]
+    return from_lists(lists, m, s, name)
+
+
+def transactions_to_tidlists(transactions, m: int, n: int) -> Instance:
+    """Horizontal format (list of item lists per transaction) -> vertical CSR."""
+    lists = [[] for _ in range(n)]
+    for x, items in enumerate(transactions):
+        for i in items:
+            lists[i].append(x)
+    return from_lists([sorted(set(l)) for l in lists], m)
+
+
+def permutations(m: int, seed: int) -> np.ndarray:
+    """The three random permutations pi_1..pi_3 of [0, m) (Sec. III-A), uint32[3, m]."""
+    out = np.empty((3, max(m, 0)), dtype=np.uint32)
+    for t in range(3):
+        out[t] = np.random.default_rng([int(seed), 0xB47, t]).permutation(m).astype(np.uint32)
+    return out
+
+
+# ---- the five workload configurations -------------------------------------
+
+CONFIGS = {
+    "cfg1": dict(kind="bernoulli", m=10_000, n=200, p=0.05, s=25, seed=1),
+    "cfg2": dict(kind="zipf", m=1_000_000, n=2_000, density=0.02, s=1_000, seed=2),
+    "cfg4_0.1": dict(kind="bernoulli", m=4_194_304, n=8_192, p=0.001, s=4_195, seed=41),
+    "cfg4_1": dict(kind="bernoulli", m=4_194_304, n=8_192, p=0.01, s=4_195, seed=42),
+    "cfg4_5": dict(kind="bernoulli", m=4_194_304, n=8_192, p=0.05, s=4_195, seed=43),
+}
+
+
+def config_instance(name: str, scale_n: int | None = None) -> Instance:
+    """Instance for a named configuration; `scale_n` truncates the item count."""
+    c = CONFIGS[name]
+    n = c["n"] if scale_n is None else min(c["n"], scale_n)
+    if c["kind"] == "bernoulli":
+        return bernoulli_tidlists(c["m"], n, c["p"], c["seed"], c["s"], name)
+    return zipf_tidlists(c["m"], n, c["density"], c["seed"], 1.0, c["s"], name)
+
+
+def batch_specs(k: int = 64, seed0: int = 1000, m_range=(1e4, 1e6), n_range=(100, 4000),
+                d_range=(0.01, 0.10)):
+    """Instance shapes of the batched workload: m log-uniform, n and density uniform."""
+    specs = []
+    for i in range(k):
+        g = np.random.default_rng([seed0 + i, 0xBA7C])
+        m = int(round(10 ** g.uniform(math.log10(m_range[0]), math.log10(m_range[1]))))
+        n = int(g.integers(n_range[0], n_range[1] + 1))
+        d = float(g.uniform(d_range[0], d_range[1]))
+        specs.append(dict(m=m, n=n, density=d, seed=seed0 + i, s=int(math.ceil(0.001 * m))))
+    return specs
+
+
+def pool_sizes(count: int, lo: int, hi: int, seed: int) -> np.ndarray:
+    """Discrete Zipf(1) set sizes on [lo, hi]: P(k) proportional to 1/k."""
+    g = np.random.default_rng([int(seed), 0x9001])
+    u = g.random(count)
+    # inverse CDF of the continuous 1/k law, floored: k = lo * (hi/lo)^u
+    return np.minimum(hi, np.floor(lo * np.exp(u * math.log((hi + 1) / lo)))).astype(np.int64)
+
+
+def pool_tidlists(count: int, universe: int, lo: int, hi: int, seed: int) -> Instance:
+    """Serving pool: `count` sets over [0, universe) with Zipf sizes, uniform members."""
+    sizes = pool_sizes(count, lo, hi, seed)
+    lists = [bernoulli_item(_item_rng(seed, i), universe, float(sizes[i]) / universe)
+             for i in range(count)]
+    return from_lists(lists, universe, 0, "pool")
