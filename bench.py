@@ -1,0 +1,324 @@
+#!/usr/bin/env python
+"""Benchmark of all-pairs support counting over BatMaps (frequent pair mining).
+
+One step = the whole hot path on one instance whose tidlists are already in
+HBM: BatMap build (sizes, 2-of-3 placement, bytes, failed insertions and
+their corrections, compare schedule), the all-pairs compare, the failure
+correction and the support-threshold compaction, ending with the number of
+frequent pairs on the host.  The metric is pair supports per second
+(n(n-1)/2 per step).
+
+Default workload: m = 1,000,000 transactions, n = 2,000 items, Zipf(1) item
+frequencies at mean density 2%, s = 1,000 (0.1% of m); inputs (160 MB of
+tids) and BatMaps (331 MB) exceed the 129 MB L2, so no flush is needed.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+    python bench.py --impl reference ...   # the CPU oracle on the same metric
+
+Prints ONE JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import datagen  # noqa: E402
+
+METRIC = "item-pair supports/sec and achieved HBM GB/s, batched vs plain, bit-exact"
+UNIT = "pair-supports/s"
+WORKLOAD_DESC = {
+    "cfg1": "plain frequent pair mining, m=10,000, n=200, Bernoulli p=0.05, s=25",
+    "cfg2": "plain all-pairs mining, m=1,000,000, n=2,000, Zipf(1) items at mean density 2%, s=1,000",
+    "cfg4_0.1": "density sweep, m=4,194,304, n=8,192, Bernoulli p=0.001",
+    "cfg4_1": "density sweep, m=4,194,304, n=8,192, Bernoulli p=0.01",
+    "cfg4_5": "density sweep, m=4,194,304, n=8,192, Bernoulli p=0.05",
+}
+OPS_PER_WORD_PAIR = 4  # LOP3, IADD, LOP3, IDP4A per 32-bit word pair
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _traffic_record():
+    """DRAM bytes per compare launch from the committed ncu summary, or None if
+    the kernel source changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "compare_traffic.json")
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    src = open(os.path.join(ROOT, "paper_1102_1003_gb300", "csrc", "compare.cu"), "rb").read()
+    if rec.get("compare_cu_sha256") != hashlib.sha256(src).hexdigest():
+        return None
+    return rec
+
+
+def _sample_pairs(n, k, seed):
+    rng = np.random.default_rng(seed)
+    i = rng.integers(0, n, k)
+    j = rng.integers(0, n - 1, k)
+    j = np.where(j >= i, j + 1, j)
+    return np.minimum(i, j), np.maximum(i, j)
+
+
+def cpu_oracle_rate(inst, seconds: float, seed: int = 0):
+    """Oracle pair supports/s on a uniform sample of the workload's pairs, run on
+    all host cores (the same single-threaded merge on disjoint blocks)."""
+    import oracle
+    cores = os.cpu_count() or 1
+    n = inst.n
+    k = 2000
+    t0 = time.perf_counter()
+    ii, jj = _sample_pairs(n, k, seed)
+    oracle.pairs_list(inst.offsets, inst.tids, ii, jj, threads=cores)
+    dt = max(time.perf_counter() - t0, 1e-6)
+    k = int(min(max(k * seconds / dt, 2000), n * (n - 1) // 2))
+    ii, jj = _sample_pairs(n, k, seed + 1)
+    t0 = time.perf_counter()
+    oracle.pairs_list(inst.offsets, inst.tids, ii, jj, threads=cores)
+    dt = time.perf_counter() - t0
+    return k / dt, cores, k, dt
+
+
+def run_reference(args, inst, rank, world):
+    if rank != 0:
+        return
+    per_step = max(2.0, min(8.0, 150.0 / max(args.steps + args.warmup, 1)))
+    for w in range(args.warmup):
+        cpu_oracle_rate(inst, per_step / 4, seed=100 + w)
+    rates, times, samples, cores = [], [], 0, 1
+    for k in range(args.steps):
+        r, cores, kk, dt = cpu_oracle_rate(inst, per_step, seed=1000 + k)
+        rates.append(r)
+        times.append(dt)
+        samples += kk
+    total_t = sum(times)
+    value = samples / total_t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic", "config": {"workload": args.workload, "desc": WORKLOAD_DESC[args.workload],
+                                        "m": inst.m, "n": inst.n, "s": inst.s, "pairs": inst.n * (inst.n - 1) // 2},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{samples} uniformly sampled pairs over {args.steps} steps "
+                                   "(single-threaded sorted merge on disjoint blocks, one per core)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_mine(args, inst, rank, world):
+    import torch
+    import paper_1102_1003_gb300 as pkg
+    from paper_1102_1003_gb300 import batmap as B
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    L = pkg.load_library()
+    perm_np = datagen.permutations(inst.m, seed=2)
+    off = torch.from_numpy(inst.offsets.astype(np.int64)).to(dev)
+    tids = torch.from_numpy(inst.tids.astype(np.int32)).to(dev)
+    perm = torch.from_numpy(perm_np.astype(np.int32)).to(dev)
+    stream = torch.cuda.current_stream()
+    npairs = inst.n * (inst.n - 1) // 2
+
+    # size the output once
+    bset = pkg.batmap_build(inst.m, off, tids, perm)
+    n_out, _ = pkg.pair_support_all(bset, inst.s)
+    info = bset.info
+    bset.free()
+    pairs_buf = torch.empty((max(n_out, 1), 3), dtype=torch.int32, device=dev)
+
+    timing = B.batmap_timing()
+    compare_ms, build_ms, compact_ms = [], [], []
+
+    def step(record):
+        bs = pkg.batmap_build(inst.m, off, tids, perm)
+        k, _ = pkg.pair_support_all(bs, inst.s, pairs=pairs_buf)
+        if record:
+            L.batmap_get_timing(bs.handle, ctypes.byref(timing))
+            compare_ms.append(timing.compare_ms)
+            build_ms.append(timing.build_ms)
+            compact_ms.append(timing.compact_ms)
+        bs.free()
+        return k
+
+    for _ in range(args.warmup):
+        step(False)
+    sampler = ClockSampler(local)
+    sampler.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = L.batmap_kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        got = step(True)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    launches = L.batmap_kernel_launches() - launches0
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    if dist:
+        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+        dist.barrier()
+    clocks = sampler.stop()
+    assert got == n_out
+
+    # end to end through the C ABI from pinned host buffers
+    h_off = torch.from_numpy(inst.offsets.astype(np.uint64).view(np.int64)).pin_memory().numpy().view(np.uint64)
+    h_tids = torch.from_numpy(inst.tids.view(np.int32)).pin_memory().numpy().view(np.uint32)
+    h_perm = torch.from_numpy(perm_np.view(np.int32)).pin_memory().numpy().view(np.uint32)
+    h_pairs = torch.empty(3 * max(n_out, 1), dtype=torch.int32).pin_memory().numpy()
+    e2e_steps = max(2, min(args.steps, 5))
+    pkg.pair_support_host(inst.m, h_off, h_tids, h_perm, inst.s, h_pairs)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        k = pkg.pair_support_host(inst.m, h_off, h_tids, h_perm, inst.s, h_pairs)
+    e2e_t = (time.perf_counter() - t0) / e2e_steps
+    assert k == n_out
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    peaks, peak_kind = _peaks()
+    value = world * npairs * args.steps / elapsed
+    cmp_s = statistics.mean(compare_ms) / 1e3
+    wp = info["word_pairs"]
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_peak = sms * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12  # Tops/s
+    achieved = OPS_PER_WORD_PAIR * wp / cmp_s / 1e12
+    logical_gbs = 8.0 * wp / cmp_s / 1e9
+    trec = _traffic_record()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": WORKLOAD_DESC[args.workload], "m": inst.m, "n": inst.n,
+                   "s": inst.s, "pairs": npairs, "tids": int(inst.tids.size), "batmap_bytes": info["bytes"],
+                   "width_classes": info["n_classes"], "l2": "inputs larger than L2 (no flush)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
+                     "frac": achieved / alu_peak, "kernel": "k_compare",
+                     "traffic": (trec["traffic_bytes_per_launch"] if trec else None),
+                     "peak_kind": f"{sms} SMs x 128 INT32 lanes x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz "
+                                  f"({peak_kind} max clock)",
+                     "algorithmic_ops": f"{OPS_PER_WORD_PAIR} x {wp:.4g} word pairs"},
+        "logical_hbm": {"achieved_GBps": logical_gbs, "peak_GBps": peaks["hbm_gbs"],
+                        "frac": logical_gbs / peaks["hbm_gbs"],
+                        "definition": "sum over pairs of 2*max(|B_i|,|B_j|) bytes / compare time (Sec. IV-A)"},
+        "phases_ms": {"build": statistics.mean(build_ms), "compare": statistics.mean(compare_ms),
+                      "correct_compact": statistics.mean(compact_ms)},
+        "frequent_pairs": n_out, "failed_insertions": info["n_failed"],
+        "gpu_launches": int(launches),
+        "e2e": {"value": npairs / e2e_t, "unit": UNIT,
+                "h2d_bytes_per_step": int(h_off.nbytes + h_tids.nbytes + h_perm.nbytes),
+                "d2h_bytes_per_step": int(12 * n_out + 8)},
+        "clocks": clocks,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        rate, cores, k, dt = cpu_oracle_rate(inst, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"{k} uniformly sampled pairs of the same workload, {dt:.1f} s "
+                                          "(single-threaded sorted merge on disjoint blocks, one per core)"}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["mine", "reference"], default="mine")
+    ap.add_argument("--workload", choices=sorted(WORKLOAD_DESC), default="cfg2")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    inst = datagen.config_instance(args.workload)
+    if args.impl == "reference":
+        run_reference(args, inst, rank, world)
+    else:
+        run_mine(args, inst, rank, world)
+
+
+if __name__ == "__main__":
+    main()

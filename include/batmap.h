@@ -1,0 +1,226 @@
+/*
+ * batmap.h -- C ABI of the GB300 BatMap library (all-pairs support counting).
+ *
+ * Problem (Sec. I of Amossen & Pagh, "A New Data Layout For Set Intersection
+ * on GPUs"): given transactions T_1..T_m over items 1..n, the support of an
+ * item pair {i, j} is |S_i intersect S_j|, where the tidlist S_i holds the
+ * transactions that contain item i.  Frequent pair mining reports every pair
+ * whose support is at least s; the paper's GPU experiment outputs the support
+ * of every pair (Sec. IV-A).
+ *
+ * Conventions for every call:
+ *   - Transaction ids are 0-based uint32 in [0, m) (the paper numbers 1..m).
+ *   - Tidlists come in CSR form: offsets[n+1] (uint64, offsets[0] = 0,
+ *     non-decreasing) and tids[offsets[n]] (uint32); the tids of item i are
+ *     tids[offsets[i] .. offsets[i+1]), strictly increasing, each < m.
+ *   - Pointers named d_* are DEVICE pointers owned by the caller; h_* are host
+ *     pointers owned by the caller.  The library never frees caller memory.
+ *   - Calls are ordered on the given CUDA stream.  Unless stated otherwise a
+ *     call returns after its work is enqueued; calls that report a count on
+ *     the host synchronise the stream.
+ *   - Every call returns BATMAP_OK (0) or a negative error code; the message
+ *     of the last error on the calling thread is batmap_last_error().  No C++
+ *     exception crosses this interface.  On error, outputs are unspecified
+ *     except where a call documents otherwise.
+ */
+#ifndef BATMAP_H
+#define BATMAP_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int batmap_status;
+
+#define BATMAP_OK 0
+#define BATMAP_ERR_ARG (-1)      /* invalid argument or malformed input data        */
+#define BATMAP_ERR_NOMEM (-2)    /* device or host allocation failed                */
+#define BATMAP_ERR_CAPACITY (-3) /* caller buffer too small; required size reported */
+#define BATMAP_ERR_CUDA (-4)     /* a CUDA runtime call or kernel failed            */
+#define BATMAP_ERR_TIMEOUT (-5)  /* a bounded device-side wait gave up              */
+#define BATMAP_ERR_INTERNAL (-6) /* internal invariant violated                     */
+
+/*
+ * Build parameters.
+ *   load_num / load_den : load factor c of the hash range, r_i = the smallest
+ *       power of two >= c |S_i|, never below r_0 (Sec. III-A; the paper uses
+ *       c = 2, giving width 3 * 2^ceil(log 2|S|) bytes, Sec. IV-A).  Any c
+ *       keeps counts exact (failed insertions are corrected).  Default 2/1.
+ *   max_loop : MaxLoop of the INSERT procedure (Sec. II-A): a placement chain
+ *       gives up after 3 * max_loop moves and its element becomes a failed
+ *       insertion.  Default 32.
+ *   min_shift : r_0 = 2^s with s the smallest shift >= min_shift such that
+ *       m <= 127 * 2^s (7-bit codes 1..127, 0x00 = empty slot; Sec. III-A).
+ *       Must be >= 7 so that every BatMap is a multiple of 384 bytes.
+ *       Default 7.
+ *   tile : 0 lets the scheduler choose compare tile shapes per width class;
+ *       1..6 forces one shape for every class (testing and autotuning).
+ *   validate : nonzero checks that tids are strictly increasing and < m per
+ *       item and that each permutation row is a bijection of [0, m); a
+ *       violation returns BATMAP_ERR_ARG.  Default 1.
+ */
+typedef struct batmap_params {
+    uint32_t load_num;
+    uint32_t load_den;
+    uint32_t max_loop;
+    uint32_t min_shift;
+    uint32_t tile;
+    uint32_t validate;
+} batmap_params;
+
+/* Opaque handle to n BatMaps built from one instance (owned by the library). */
+typedef struct batmap_set batmap_set;
+
+/* Summary of a built set (host struct filled by batmap_get_info). */
+typedef struct batmap_info {
+    uint32_t m;              /* transactions                                   */
+    uint32_t n;              /* items                                          */
+    uint32_t shift;          /* s: codes are (pi >> s) + 1                     */
+    uint32_t r0;             /* 2^s, the smallest hash range                   */
+    uint64_t bytes;          /* total BatMap bytes, sum of 3 r_i               */
+    uint64_t n_elements;     /* total tids, offsets[n]                         */
+    uint64_t n_failed;       /* failed insertions, sum of |F_i|                */
+    uint64_t n_corrections;  /* correction entries (one per failed common tid) */
+    uint64_t n_work_units;   /* compare work units scheduled                   */
+    uint32_t n_classes;      /* distinct BatMap widths                         */
+    uint32_t reserved;
+    double word_pairs;       /* sum over pairs i<j of max(|B_i|,|B_j|)/4       */
+} batmap_info;
+
+/* Fills *p with the defaults documented above. */
+void batmap_default_params(batmap_params *p);
+
+/* Message of the last error raised on the calling thread ("" if none). */
+const char *batmap_last_error(void);
+
+/*
+ * Build the BatMaps of all n items (Sec. II and Sec. III-A):
+ *   - sizes r_i, widths |B_i| = 3 r_i bytes, and the width-sorted order of
+ *     the items (Sec. III-C);
+ *   - places every tid of S_i in two of its three hash tables with a
+ *     parallel generalisation of the cuckoo INSERT procedure (Sec. II-A);
+ *   - writes the 8-bit elements: indicator bit << 7 | ((pi_t(x) >> s) + 1),
+ *     0x00 for empty slots, at h_t^(i)(x) = |B_0| floor((pi_t(x) mod r_i)/r_0)
+ *     + (pi_t(x) mod r_0) + (t-1) r_0 (Sec. III-A);
+ *   - records failed insertions F_i and precomputes their correction entries
+ *     (Sec. III-C, "Failed insertions").
+ * Arguments:
+ *   p         : parameters, or NULL for the defaults.
+ *   m, n      : transactions (1 <= m <= 2^30) and items (n >= 0).
+ *   d_offsets : device uint64[n+1], CSR offsets.
+ *   d_tids    : device uint32[offsets[n]], CSR tids (may be NULL when empty).
+ *   d_perm    : device uint32[3*m]; row t (t = 0, 1, 2) is the permutation
+ *               pi_{t+1} of [0, m) used by the layout hash.
+ *   stream    : CUDA stream for all work of this call.
+ *   out       : receives the new handle; release it with batmap_free.
+ * The call synchronises the stream (sizes are needed on the host).  The
+ * caller may free its input buffers once the call returns.
+ */
+batmap_status batmap_build(const batmap_params *p, uint32_t m, uint32_t n,
+                           const uint64_t *d_offsets, const uint32_t *d_tids,
+                           const uint32_t *d_perm, cudaStream_t stream, batmap_set **out);
+
+/* Release a handle and all device memory it owns (NULL is ignored). */
+void batmap_free(batmap_set *set);
+
+/* Copy the summary of a built set into *info. */
+batmap_status batmap_get_info(const batmap_set *set, batmap_info *info);
+
+/*
+ * Copy the built layout to host buffers (used to check layouts against the
+ * definition).  Any pointer may be NULL to skip that output.
+ *   h_bytes        : uint8[info.bytes], all BatMaps, width-sorted order.
+ *   h_byte_offset  : uint64[n], byte offset of item i's BatMap (original id).
+ *   h_range        : uint32[n], r_i of item i.
+ *   h_fail_offsets : uint64[n+1], CSR offsets of the failed tids per item.
+ *   h_fail_tids    : uint32[info.n_failed], F_i sorted ascending per item.
+ * Synchronises the set's stream.
+ */
+batmap_status batmap_export_layout(const batmap_set *set, uint8_t *h_bytes,
+                                   uint64_t *h_byte_offset, uint32_t *h_range,
+                                   uint64_t *h_fail_offsets, uint32_t *h_fail_tids);
+
+/*
+ * Support of every item pair and the frequent pairs (Sec. I problem
+ * statement; Sec. III-B/C all-pairs comparison, failure correction).
+ *   s       : support threshold; pairs with support >= s are reported.
+ *   d_pairs : device uint32[3*cap]: triples (i, j, support) with original
+ *             item ids i < j, in lexicographic (i, j) order.  May be NULL
+ *             when cap == 0.
+ *   cap     : capacity of d_pairs in triples.
+ *   n_out   : host; receives the number of qualifying pairs.  If it exceeds
+ *             cap, the first cap triples are written and BATMAP_ERR_CAPACITY
+ *             is returned.
+ *   d_full  : optional device uint32[n(n-1)/2]: support of every pair i < j,
+ *             packed row-major upper triangle, index i*n - i(i+1)/2 + j-i-1.
+ *             NULL to skip.
+ * Synchronises the stream (to report n_out).
+ */
+batmap_status pair_support_all(batmap_set *set, uint32_t s, uint32_t *d_pairs, uint64_t cap,
+                               uint64_t *n_out, uint32_t *d_full, cudaStream_t stream);
+
+/*
+ * End-to-end convenience for callers holding their data on the HOST: copies
+ * the CSR tidlists and permutations to the device, builds the BatMaps, counts
+ * all pairs, and copies the frequent pairs back.
+ *   h_offsets, h_tids, h_perm : host inputs as in batmap_build (pinned
+ *       memory gives the fastest copies).
+ *   h_pairs, cap, n_out : host output triples as in pair_support_all.
+ * Synchronises the stream; device memory is released before returning.
+ */
+batmap_status pair_support_host(const batmap_params *p, uint32_t m, uint32_t n,
+                                const uint64_t *h_offsets, const uint32_t *h_tids,
+                                const uint32_t *h_perm, uint32_t s, uint32_t *h_pairs,
+                                uint64_t cap, uint64_t *n_out, cudaStream_t stream);
+
+/*
+ * Device-side durations of the most recent batmap_build / pair_support_all
+ * on a set, measured with CUDA events recorded on the call's stream around
+ * each phase (milliseconds; 0 for a phase that did not run).
+ */
+typedef struct batmap_timing {
+    float build_ms;     /* whole batmap_build, first to last enqueued operation */
+    float place_ms;     /* 2-of-3 placement kernel                              */
+    float finalize_ms;  /* byte writing + failure lists + correction entries    */
+    float compare_ms;   /* the persistent all-pairs compare launch              */
+    float compact_ms;   /* failure correction + threshold compaction            */
+    float pairs_ms;     /* whole pair_support_all                               */
+} batmap_timing;
+
+/* Copy the phase durations of the set's most recent calls into *t. */
+batmap_status batmap_get_timing(const batmap_set *set, batmap_timing *t);
+
+/* Number of kernels this library has launched in the process so far (a
+ * diagnostic counter; differences around a region count its launches). */
+uint64_t batmap_kernel_launches(void);
+
+/* Per-instance outputs of pair_support_batch (host struct). */
+typedef struct batmap_out {
+    uint32_t *d_pairs; /* device uint32[3*cap] triples, as in pair_support_all */
+    uint64_t cap;      /* capacity in triples                                 */
+    uint64_t n_out;    /* filled in: qualifying pairs of this instance        */
+    uint32_t *d_full;  /* optional packed upper triangle, or NULL             */
+} batmap_out;
+
+/*
+ * Many independent mining instances in one pass: the compare work of all k
+ * sets runs in ONE persistent launch that pulls (instance, tile, k-range)
+ * units from a shared queue, followed by the per-instance correction and
+ * compaction.  Results equal k separate pair_support_all calls.
+ *   sets : k built handles.   s : host uint32[k] thresholds.
+ *   outs : host batmap_out[k]; n_out is filled in for each instance.
+ * Returns BATMAP_ERR_CAPACITY if any instance overflowed its buffer (that
+ * instance's first cap triples are written).  Synchronises the stream.
+ */
+batmap_status pair_support_batch(batmap_set *const *sets, const uint32_t *s, uint32_t k,
+                                 batmap_out *outs, cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BATMAP_H */

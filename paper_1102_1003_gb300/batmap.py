@@ -1,0 +1,256 @@
+"""Python binding of libbatmap.so (argument marshalling only).
+
+Every function here has the name of the C entry point it calls (include/
+batmap.h).  Device buffers are torch CUDA tensors, streams are torch CUDA
+streams; all computation runs in the library's CUDA kernels.  There is no CPU
+fallback: if the library is missing, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libbatmap.so")
+
+BATMAP_OK = 0
+BATMAP_ERR_ARG = -1
+BATMAP_ERR_NOMEM = -2
+BATMAP_ERR_CAPACITY = -3
+BATMAP_ERR_CUDA = -4
+BATMAP_ERR_TIMEOUT = -5
+BATMAP_ERR_INTERNAL = -6
+
+EXPORTED = [
+    "batmap_default_params", "batmap_last_error", "batmap_build", "batmap_free",
+    "batmap_get_info", "batmap_export_layout", "pair_support_all", "pair_support_host",
+    "pair_support_batch", "batmap_get_timing", "batmap_kernel_launches",
+]
+
+
+class batmap_params(ctypes.Structure):
+    _fields_ = [("load_num", ctypes.c_uint32), ("load_den", ctypes.c_uint32),
+                ("max_loop", ctypes.c_uint32), ("min_shift", ctypes.c_uint32),
+                ("tile", ctypes.c_uint32), ("validate", ctypes.c_uint32)]
+
+
+class batmap_info(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_uint32), ("n", ctypes.c_uint32), ("shift", ctypes.c_uint32),
+                ("r0", ctypes.c_uint32), ("bytes", ctypes.c_uint64),
+                ("n_elements", ctypes.c_uint64), ("n_failed", ctypes.c_uint64),
+                ("n_corrections", ctypes.c_uint64), ("n_work_units", ctypes.c_uint64),
+                ("n_classes", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("word_pairs", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+class batmap_timing(ctypes.Structure):
+    _fields_ = [("build_ms", ctypes.c_float), ("place_ms", ctypes.c_float),
+                ("finalize_ms", ctypes.c_float), ("compare_ms", ctypes.c_float),
+                ("compact_ms", ctypes.c_float), ("pairs_ms", ctypes.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class batmap_out(ctypes.Structure):
+    _fields_ = [("d_pairs", ctypes.c_void_p), ("cap", ctypes.c_uint64),
+                ("n_out", ctypes.c_uint64), ("d_full", ctypes.c_void_p)]
+
+
+class BatmapError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"batmap error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libbatmap.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    L = ctypes.CDLL(path)
+    vp, u32, u64 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64
+    L.batmap_default_params.argtypes = [ctypes.POINTER(batmap_params)]
+    L.batmap_default_params.restype = None
+    L.batmap_last_error.argtypes = []
+    L.batmap_last_error.restype = ctypes.c_char_p
+    L.batmap_build.argtypes = [ctypes.POINTER(batmap_params), u32, u32, vp, vp, vp, vp,
+                               ctypes.POINTER(vp)]
+    L.batmap_build.restype = ctypes.c_int
+    L.batmap_free.argtypes = [vp]
+    L.batmap_free.restype = None
+    L.batmap_get_info.argtypes = [vp, ctypes.POINTER(batmap_info)]
+    L.batmap_get_info.restype = ctypes.c_int
+    L.batmap_export_layout.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.batmap_export_layout.restype = ctypes.c_int
+    L.pair_support_all.argtypes = [vp, u32, vp, u64, ctypes.POINTER(u64), vp, vp]
+    L.pair_support_all.restype = ctypes.c_int
+    L.pair_support_host.argtypes = [ctypes.POINTER(batmap_params), u32, u32, vp, vp, vp, u32, vp,
+                                    u64, ctypes.POINTER(u64), vp]
+    L.pair_support_host.restype = ctypes.c_int
+    L.pair_support_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(u32), u32,
+                                     ctypes.POINTER(batmap_out), vp]
+    L.pair_support_batch.restype = ctypes.c_int
+    L.batmap_get_timing.argtypes = [vp, ctypes.POINTER(batmap_timing)]
+    L.batmap_get_timing.restype = ctypes.c_int
+    L.batmap_kernel_launches.argtypes = []
+    L.batmap_kernel_launches.restype = u64
+    _lib = L
+    return L
+
+
+def _check(rc, allow=()):
+    if rc != BATMAP_OK and rc not in allow:
+        raise BatmapError(rc, load_library().batmap_last_error().decode())
+    return rc
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def batmap_default_params(**overrides) -> batmap_params:
+    p = batmap_params()
+    load_library().batmap_default_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, int(v))
+    return p
+
+
+class BatMapSet:
+    """Owning wrapper of a built batmap_set handle."""
+
+    def __init__(self, handle, m, n):
+        self.handle = handle
+        self.m = m
+        self.n = n
+
+    def __del__(self):
+        self.free()
+
+    def free(self):
+        if getattr(self, "handle", None):
+            load_library().batmap_free(self.handle)
+            self.handle = None
+
+    @property
+    def info(self) -> dict:
+        return batmap_get_info(self)
+
+
+def batmap_build(m: int, offsets, tids, perm, params: batmap_params | None = None, stream=None) -> BatMapSet:
+    """Build the BatMaps of n = offsets.numel() - 1 items from device CSR tidlists.
+
+    offsets: cuda uint64 (int64) tensor [n+1]; tids: cuda int32/uint32 [T];
+    perm: cuda int32/uint32 [3, m] (three permutations of [0, m))."""
+    L = load_library()
+    n = int(offsets.numel()) - 1
+    h = ctypes.c_void_p()
+    pp = ctypes.byref(params) if params is not None else None
+    _check(L.batmap_build(pp, int(m), n, _ptr(offsets), _ptr(tids) if tids.numel() else None,
+                          _ptr(perm), _stream_handle(stream), ctypes.byref(h)))
+    return BatMapSet(h, int(m), n)
+
+
+def batmap_free(bset: BatMapSet):
+    bset.free()
+
+
+def batmap_get_info(bset: BatMapSet) -> dict:
+    info = batmap_info()
+    _check(load_library().batmap_get_info(bset.handle, ctypes.byref(info)))
+    return info.as_dict()
+
+
+def batmap_get_timing(bset: BatMapSet) -> dict:
+    """Device durations (ms) of the set's most recent build / pair_support_all phases."""
+    t = batmap_timing()
+    _check(load_library().batmap_get_timing(bset.handle, ctypes.byref(t)))
+    return t.as_dict()
+
+
+def batmap_kernel_launches() -> int:
+    return int(load_library().batmap_kernel_launches())
+
+
+def batmap_export_layout(bset: BatMapSet) -> dict:
+    """Host copies of the built layout (for checking it against the definition)."""
+    info = batmap_get_info(bset)
+    n = bset.n
+    out = dict(bytes=np.zeros(info["bytes"], np.uint8), byte_offset=np.zeros(n, np.uint64),
+               range=np.zeros(n, np.uint32), fail_offsets=np.zeros(n + 1, np.uint64),
+               fail_tids=np.zeros(max(info["n_failed"], 1), np.uint32), info=info)
+    _check(load_library().batmap_export_layout(
+        bset.handle, out["bytes"].ctypes.data, out["byte_offset"].ctypes.data, out["range"].ctypes.data,
+        out["fail_offsets"].ctypes.data, out["fail_tids"].ctypes.data))
+    out["fail_tids"] = out["fail_tids"][:info["n_failed"]]
+    return out
+
+
+def pair_support_all(bset: BatMapSet, s: int, pairs=None, full=None, stream=None):
+    """Supports of all pairs; returns (n_out, pairs) with pairs a cuda int32 [k, 3] view
+    (i, j, support) of the first min(n_out, cap) qualifying pairs.  If `pairs` is None a
+    buffer is sized by a counting call first.  `full` (optional) receives the packed
+    upper triangle."""
+    import torch
+    L = load_library()
+    n_out = ctypes.c_uint64(0)
+    st = _stream_handle(stream)
+    if pairs is None:
+        rc = L.pair_support_all(bset.handle, int(s), None, 0, ctypes.byref(n_out), _ptr(full), st)
+        _check(rc, allow=(BATMAP_ERR_CAPACITY,))
+        pairs = torch.empty((max(int(n_out.value), 1), 3), dtype=torch.int32, device="cuda")
+    cap = pairs.numel() // 3
+    rc = L.pair_support_all(bset.handle, int(s), _ptr(pairs), cap, ctypes.byref(n_out), _ptr(full), st)
+    _check(rc, allow=(BATMAP_ERR_CAPACITY,))
+    k = min(int(n_out.value), cap)
+    return int(n_out.value), pairs.view(-1, 3)[:k]
+
+
+def pair_support_batch(sets, s_list, pairs_list, full_list=None, stream=None):
+    """One batched call over several sets; returns the per-instance n_out list."""
+    L = load_library()
+    k = len(sets)
+    handles = (ctypes.c_void_p * k)(*[b.handle for b in sets])
+    svals = (ctypes.c_uint32 * k)(*[int(x) for x in s_list])
+    outs = (batmap_out * k)()
+    for q in range(k):
+        outs[q].d_pairs = pairs_list[q].data_ptr() if pairs_list[q] is not None else None
+        outs[q].cap = (pairs_list[q].numel() // 3) if pairs_list[q] is not None else 0
+        outs[q].d_full = (full_list[q].data_ptr() if full_list is not None and full_list[q] is not None
+                          else None)
+    rc = L.pair_support_batch(handles, svals, k, outs, _stream_handle(stream))
+    _check(rc, allow=(BATMAP_ERR_CAPACITY,))
+    return [int(outs[q].n_out) for q in range(k)]
+
+
+def pair_support_host(m: int, offsets: np.ndarray, tids: np.ndarray, perm: np.ndarray, s: int,
+                      pairs_out: np.ndarray, params: batmap_params | None = None, stream=None) -> int:
+    """End to end from host (preferably pinned) numpy buffers; returns n_out."""
+    L = load_library()
+    n = offsets.size - 1
+    n_out = ctypes.c_uint64(0)
+    pp = ctypes.byref(params) if params is not None else None
+    rc = L.pair_support_host(pp, int(m), n, offsets.ctypes.data, tids.ctypes.data if tids.size else None,
+                             perm.ctypes.data, int(s), pairs_out.ctypes.data, pairs_out.size // 3,
+                             ctypes.byref(n_out), _stream_handle(stream))
+    _check(rc, allow=(BATMAP_ERR_CAPACITY,))
+    return int(n_out.value)

@@ -1,0 +1,166 @@
+// Batched form: many independent mining instances in ONE persistent compare
+// launch, captured with the per-instance correction and compaction into a
+// CUDA graph that is replayed while the same sets and outputs are used.
+//
+// The work units of all instances are merged into one queue ordered longest
+// first, so small instances fill the SMs left idle by large ones and the
+// tail of one instance overlaps the work of the others.
+#include <algorithm>
+#include <memory>
+#include <mutex>
+#include <string>
+
+#include "common.cuh"
+#include "compare.cuh"
+
+namespace bm {
+
+void enqueue_correct_compact(batmap_set *S, uint32_t *C, uint32_t s, uint32_t *d_pairs, uint64_t cap,
+                             uint64_t *d_total, cudaStream_t st);
+void prepare_compaction(batmap_set *S);
+
+struct BatchPlan {
+    std::vector<uint64_t> key;
+    std::vector<uint32_t *> C;
+    DevBuf<InstView> d_views;
+    DevBuf<WorkUnit> d_units;
+    DevBuf<uint32_t> d_counter;
+    DevBuf<uint64_t> d_totals;
+    uint32_t nunits = 0;
+    cudaStream_t stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    ~BatchPlan() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+    }
+};
+
+static std::mutex g_batch_mu;
+static std::unique_ptr<BatchPlan> g_plan;
+
+static std::vector<uint64_t> plan_key(batmap_set *const *sets, const uint32_t *s, uint32_t k,
+                                      const batmap_out *outs, cudaStream_t st) {
+    std::vector<uint64_t> key;
+    key.push_back((uint64_t)(uintptr_t)st);
+    key.push_back(k);
+    for (uint32_t q = 0; q < k; q++) {
+        key.push_back(sets[q]->gen);
+        key.push_back(s[q]);
+        key.push_back((uint64_t)(uintptr_t)outs[q].d_pairs);
+        key.push_back(outs[q].cap);
+        key.push_back((uint64_t)(uintptr_t)outs[q].d_full);
+    }
+    return key;
+}
+
+static void enqueue_batch(BatchPlan *P, batmap_set *const *sets, const uint32_t *s, uint32_t k,
+                          const batmap_out *outs, cudaStream_t st) {
+    for (uint32_t q = 0; q < k; q++) {
+        const uint64_t n = sets[q]->n;
+        if (n > 1) BM_CUDA(cudaMemsetAsync(P->C[q], 0, n * (n - 1) / 2 * sizeof(uint32_t), st));
+    }
+    BM_CUDA(cudaMemsetAsync(P->d_counter.p, 0, sizeof(uint32_t), st));
+    launch_compare(P->d_views.p, P->d_units.p, P->nunits, P->d_counter.p,
+                   std::min<uint32_t>(P->nunits, (uint32_t)device_sms()), st);
+    for (uint32_t q = 0; q < k; q++)
+        enqueue_correct_compact(sets[q], P->C[q], s[q], outs[q].d_pairs, outs[q].cap, P->d_totals.p + q, st);
+}
+
+static BatchPlan *make_plan(batmap_set *const *sets, const uint32_t *s, uint32_t k, const batmap_out *outs,
+                            cudaStream_t st, std::vector<uint64_t> key) {
+    auto P = std::make_unique<BatchPlan>();
+    P->key = std::move(key);
+    P->stream = st;
+    std::vector<InstView> views(k);
+    std::vector<WorkUnit> units;
+    P->C.resize(k);
+    for (uint32_t q = 0; q < k; q++) {
+        batmap_set *S = sets[q];
+        const uint64_t n = S->n;
+        uint32_t *C = outs[q].d_full;
+        if (!C) {
+            S->d_C.ensure(n * (n - 1) / 2);
+            C = S->d_C.p;
+        }
+        P->C[q] = C;
+        views[q] = InstView{reinterpret_cast<const uint4 *>(S->d_bm.p), S->d_line_off.p, S->d_wshift.p,
+                            S->d_order.p, C, S->n, 0};
+        for (WorkUnit u : S->units) {
+            u.inst = q;
+            units.push_back(u);
+        }
+        prepare_compaction(S);
+    }
+    sort_units(&units);
+    P->nunits = (uint32_t)units.size();
+    P->d_views.alloc(k);
+    P->d_units.alloc(units.size());
+    P->d_counter.alloc(1);
+    P->d_totals.alloc(k);
+    BM_CUDA(cudaMemcpyAsync(P->d_views.p, views.data(), k * sizeof(InstView), cudaMemcpyHostToDevice, st));
+    if (!units.empty())
+        BM_CUDA(cudaMemcpyAsync(P->d_units.p, units.data(), units.size() * sizeof(WorkUnit),
+                                cudaMemcpyHostToDevice, st));
+    BM_CUDA(cudaStreamSynchronize(st));
+    prepare_compare();
+
+    // capture the whole batch (zeroing, one compare launch, k compactions)
+    cudaStream_t cap_st = st;
+    bool own_stream = false;
+    if (cap_st == nullptr) {  // the legacy default stream cannot be captured
+        BM_CUDA(cudaStreamCreateWithFlags(&cap_st, cudaStreamNonBlocking));
+        own_stream = true;
+    }
+    try {
+        BM_CUDA(cudaStreamBeginCapture(cap_st, cudaStreamCaptureModeThreadLocal));
+        try {
+            enqueue_batch(P.get(), sets, s, k, outs, cap_st);
+        } catch (...) {
+            cudaGraph_t g = nullptr;
+            cudaStreamEndCapture(cap_st, &g);
+            if (g) cudaGraphDestroy(g);
+            throw;
+        }
+        BM_CUDA(cudaStreamEndCapture(cap_st, &P->graph));
+        BM_CUDA(cudaGraphInstantiate(&P->exec, P->graph, 0));
+    } catch (...) {
+        if (own_stream) cudaStreamDestroy(cap_st);
+        throw;
+    }
+    if (own_stream) cudaStreamDestroy(cap_st);
+    return P.release();
+}
+
+void run_batch(batmap_set *const *sets, const uint32_t *s, uint32_t k, batmap_out *outs, cudaStream_t st) {
+    BM_REQUIRE(sets && s && outs, BATMAP_ERR_ARG, "NULL argument");
+    for (uint32_t q = 0; q < k; q++) {
+        BM_REQUIRE(sets[q], BATMAP_ERR_ARG, "NULL set in batch");
+        BM_REQUIRE(outs[q].cap == 0 || outs[q].d_pairs, BATMAP_ERR_ARG, "d_pairs is NULL with cap > 0");
+    }
+    if (k == 0) return;
+    std::lock_guard<std::mutex> lock(g_batch_mu);
+    auto key = plan_key(sets, s, k, outs, st);
+    if (!g_plan || g_plan->key != key) {
+        g_plan.reset();
+        g_plan.reset(make_plan(sets, s, k, outs, st, std::move(key)));
+    }
+    BatchPlan *P = g_plan.get();
+    BM_CUDA(cudaGraphLaunch(P->exec, st));
+    std::vector<uint64_t> totals(k);
+    BM_CUDA(cudaMemcpyAsync(totals.data(), P->d_totals.p, k * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    BM_CUDA(cudaStreamSynchronize(st));
+    bool overflow = false;
+    for (uint32_t q = 0; q < k; q++) {
+        outs[q].n_out = totals[q];
+        overflow |= totals[q] > outs[q].cap;
+    }
+    if (overflow) throw Error{BATMAP_ERR_CAPACITY, "an instance's d_pairs is too small (see n_out)"};
+}
+
+void release_batch_plan() {
+    std::lock_guard<std::mutex> lock(g_batch_mu);
+    g_plan.reset();
+}
+
+}  // namespace bm

@@ -1,0 +1,182 @@
+// Shared helpers of the CUDA path: error plumbing, device utilities, layout
+// arithmetic (Sec. III-A) and the internal representation of a built set.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/batmap.h"
+
+namespace bm {
+
+// ---- error plumbing ---------------------------------------------------------
+
+void set_error(const std::string &msg);
+
+struct Error {
+    batmap_status code;
+    std::string msg;
+};
+
+#define BM_CUDA(call)                                                                       \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess) {                                                            \
+            throw ::bm::Error{e_ == cudaErrorMemoryAllocation ? BATMAP_ERR_NOMEM            \
+                                                              : BATMAP_ERR_CUDA,            \
+                              std::string(#call) + ": " + cudaGetErrorString(e_)};         \
+        }                                                                                   \
+    } while (0)
+
+void count_launch();
+#define BM_CHECK_LAUNCH()             \
+    do {                              \
+        BM_CUDA(cudaGetLastError());  \
+        ::bm::count_launch();         \
+    } while (0)
+
+#define BM_REQUIRE(cond, code, msg)                                                         \
+    do {                                                                                    \
+        if (!(cond)) throw ::bm::Error{(code), (msg)};                                      \
+    } while (0)
+
+// RAII device buffer (cudaMalloc / cudaFree).
+template <typename T>
+struct DevBuf {
+    T *p = nullptr;
+    size_t n = 0;
+    DevBuf() = default;
+    explicit DevBuf(size_t count) { alloc(count); }
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    DevBuf(DevBuf &&o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+    DevBuf &operator=(DevBuf &&o) noexcept {
+        if (this != &o) { release(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+        return *this;
+    }
+    ~DevBuf() { release(); }
+    void alloc(size_t count) {
+        release();
+        if (count) BM_CUDA(cudaMalloc(&p, count * sizeof(T)));
+        n = count;
+    }
+    void ensure(size_t count) { if (count > n) alloc(count); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    size_t bytes() const { return n * sizeof(T); }
+};
+
+// Events bracketing phases of a call on its stream.
+struct PhaseEvents {
+    static constexpr int N = 8;
+    cudaEvent_t ev[N] = {};
+    bool ok = false;
+    void create() {
+        if (ok) return;
+        for (int i = 0; i < N; i++) BM_CUDA(cudaEventCreate(&ev[i]));
+        ok = true;
+    }
+    void record(int i, cudaStream_t st) { BM_CUDA(cudaEventRecord(ev[i], st)); }
+    float ms(int a, int b) const {
+        float t = 0.f;
+        if (ok && cudaEventElapsedTime(&t, ev[a], ev[b]) != cudaSuccess) {
+            cudaGetLastError();
+            t = 0.f;
+        }
+        return t;
+    }
+    ~PhaseEvents() {
+        if (ok)
+            for (int i = 0; i < N; i++) cudaEventDestroy(ev[i]);
+    }
+};
+
+// ---- layout arithmetic (Sec. III-A) ----------------------------------------
+
+// Slot of pi = pi_t(x) in table t of a BatMap with range r (power of two,
+// >= r0 = 2^shift): |B_0| floor((pi mod r)/r0) + (pi mod r0) + t r0.
+__host__ __device__ __forceinline__ uint64_t slot_of(uint32_t t, uint32_t pi, uint32_t r,
+                                                    uint32_t shift) {
+    uint32_t r0 = 1u << shift;
+    uint32_t h = pi & (r - 1u);
+    return 3ull * r0 * (uint64_t)(h >> shift) + (h & (r0 - 1u)) + (uint64_t)t * r0;
+}
+
+// 8-bit element: indicator in bit 7, code (pi >> shift) + 1 in bits 0..6.
+__host__ __device__ __forceinline__ uint32_t element_byte(uint32_t pi, uint32_t shift,
+                                                         uint32_t ind) {
+    return (ind << 7) | ((pi >> shift) + 1u);
+}
+
+// ---- compare work units ----------------------------------------------------
+
+// One unit of the all-pairs compare: rows [r0, r1) x columns [c0, c1) of the
+// width-sorted item order, word range [k0, k0 + klen) of the column width.
+// Rows are never wider than columns; columns of a unit share one width.
+struct WorkUnit {
+    uint32_t r0, r1, c0, c1;
+    uint32_t k0, klen;
+    uint32_t inst;   // instance index (batched launches), 0 otherwise
+    uint32_t shape;  // tile shape index (0-based)
+};
+static_assert(sizeof(WorkUnit) == 32, "WorkUnit layout");
+
+// Per-instance device view used by the compare kernel (batched form indexes
+// an array of these by WorkUnit::inst).
+struct InstView {
+    const uint4 *bm;          // BatMap bytes of this instance, as 16-byte chunks
+    const uint32_t *line_off; // [n] sorted order: byte offset / 128 of each BatMap
+    const uint32_t *wshift;   // [n] sorted order: e with |B|/4 words = 3 * 2^e
+    const uint32_t *order;    // [n] sorted position -> original item id
+    uint32_t *C;              // packed upper triangle of supports (original ids)
+    uint32_t n;
+    uint32_t pad;
+};
+
+}  // namespace bm
+
+// The library-owned handle behind the opaque C type.
+struct batmap_set {
+    batmap_params params{};
+    uint32_t m = 0, n = 0, shift = 0, r0 = 0;
+    uint64_t n_elements = 0, bytes = 0, n_failed = 0, n_corr = 0;
+    double word_pairs = 0.0;
+    uint64_t gen = 0;  // unique build id (batch plans key on it)
+    cudaStream_t stream = nullptr;
+
+    // host metadata
+    std::vector<uint32_t> range;          // r_i, original order
+    std::vector<uint32_t> order;          // sorted position -> original id
+    std::vector<uint32_t> rank;           // original id -> sorted position
+    std::vector<uint64_t> byte_off;       // byte offset of BatMap, sorted order
+    std::vector<uint32_t> wshift_sorted;  // e per sorted position
+    std::vector<uint32_t> class_begin;    // sorted positions where a width class starts (+ n)
+    std::vector<bm::WorkUnit> units;      // compare schedule, longest first
+
+    // device data
+    bm::DevBuf<uint8_t> d_bm;             // all BatMaps, width-sorted order
+    bm::DevBuf<uint32_t> d_line_off;      // [n] sorted
+    bm::DevBuf<uint32_t> d_wshift;        // [n] sorted
+    bm::DevBuf<uint32_t> d_order;         // [n]
+    bm::DevBuf<bm::WorkUnit> d_units;
+    bm::DevBuf<uint32_t> d_corr;          // [2 * n_corr] (i, j) original ids, i < j
+    bm::DevBuf<uint64_t> d_fail_off;      // [n+1] failed tids per item (CSR)
+    bm::DevBuf<uint32_t> d_fail_tid;      // [n_failed], sorted per item
+
+    // timing of the most recent calls
+    bm::PhaseEvents build_ev, pairs_ev;
+    batmap_timing timing{};
+
+    // scratch reused across pair_support_all calls
+    bm::DevBuf<uint32_t> d_C;             // packed upper triangle when no d_full
+    bm::DevBuf<uint32_t> d_counters;      // work-queue counter
+    bm::DevBuf<bm::InstView> d_view;      // device copy of this set's InstView
+    bm::DevBuf<uint64_t> d_blocksums;     // compaction block counts / offsets
+    bm::DevBuf<uint64_t> d_total;         // compaction total
+};

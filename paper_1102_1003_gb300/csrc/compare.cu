@@ -1,0 +1,357 @@
+// The all-pairs BatMap compare kernel and its schedule (Sec. III-A/B/C).
+//
+// Counting rule (Sec. II, Fig. 3): a slot counts iff the 7 element bits of
+// the two bytes agree and at least one indicator bit is set; the bottom byte
+// 0x00 never counts.  Four slots are compared per 32-bit word:
+//     L = (x ^ y) & 0x7F7F7F7F      element bits equal  <=>  lane of L == 0
+//     t = L + 0x7F7F7F7F            lane bit 7 = [element bits differ]; no
+//                                   carry leaves a lane (0x7F + 0x7F < 0x100)
+//     q = ~t & (xi | yi)            xi, yi = indicator bits (x & 0x80808080)
+//     acc += dp4a(q, 0x01010101)    adds 128 per counted slot
+// This equals the paper's p / p' formulation (Sec. III-A) lane by lane; the
+// indicator masks xi, yi are formed once per loaded word and reused across
+// the 8 partners of the register tile.
+//
+// Sizes of different width (Sec. II, Fig. 1): the BatMap of the narrower row
+// item i is compared cyclically, word k of the wider column item j against
+// word k mod (|B_i|/4) of item i.  Widths are 3 * 2^e words, so the wrap is
+// ((k >> e) % 3) << e | (k & (2^e - 1)).
+//
+// Work decomposition (GB300 design, replacing the paper's 16 x 16 work groups
+// and host-side k x k blocks, Sec. III-B/C): items are sorted by width; the
+// columns of a tile come from ONE width class, the rows are any items before
+// them in sorted order; each (tile, word range) is a work unit; a persistent
+// grid pulls units (longest first) from an atomic counter and adds its
+// partial counts into the packed upper triangle with atomics (integer sums
+// are exact in any order).
+#include <algorithm>
+#include <cmath>
+
+#include "compare.cuh"
+
+namespace bm {
+
+const ShapeDesc SHAPES[NUM_SHAPES] = {
+    {1, 128, 128, 8, 32, 3, 1.00},
+    {2, 256, 64, 8, 32, 3, 0.98},
+    {3, 512, 32, 8, 32, 2, 0.95},
+    {4, 1024, 16, 8, 16, 2, 0.92},
+    {5, 2048, 8, 8, 8, 2, 0.88},
+    {6, 2048, 4, 4, 8, 2, 0.80},
+};
+
+int device_sms() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        BM_CUDA(cudaGetDevice(&dev));
+        BM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    return sms;
+}
+
+// ---- device helpers -----------------------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, bool valid) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src),
+                 "r"(valid ? 16 : 0));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+__device__ __forceinline__ uint32_t wrap_word(uint32_t k, uint32_t e) {
+    uint32_t q = k >> e;
+    return ((q % 3u) << e) | (k & ((1u << e) - 1u));
+}
+
+__device__ __forceinline__ uint32_t lane_word(const uint4 &v, int kk) {
+    return kk == 0 ? v.x : kk == 1 ? v.y : kk == 2 ? v.z : v.w;
+}
+
+// One 32-bit word pair: adds 128 per counted slot to acc.
+__device__ __forceinline__ uint32_t swar_step(uint32_t acc, uint32_t x, uint32_t xi, uint32_t y,
+                                              uint32_t yi) {
+    uint32_t l = (x ^ y) & 0x7F7F7F7Fu;
+    uint32_t t = l + 0x7F7F7F7Fu;
+    uint32_t q = ~t & (xi | yi);
+    return __dp4a(q, 0x01010101u, acc);
+}
+
+template <int TR_T, int TC_T, int MC, int KC, int STAGES>
+struct Tile {
+    static constexpr int MR = 8;
+    static constexpr int NT = TR_T * TC_T;
+    static constexpr int TR = MR * TR_T;
+    static constexpr int TC = MC * TC_T;
+    static constexpr int CPR = KC / 4;  // 16-byte chunks per row per stage
+    static constexpr int SWB = CPR < 8 ? CPR : 8;
+    static constexpr int SWS = CPR >= 8 ? 0 : (CPR == 4 ? 1 : (CPR == 2 ? 2 : 3));
+    static constexpr int ROW_CHUNKS = TR * CPR;
+    static constexpr int COL_CHUNKS = TC * CPR;
+    static constexpr int STAGE_CHUNKS = ROW_CHUNKS + COL_CHUNKS;
+    static constexpr size_t SMEM = (size_t)STAGES * STAGE_CHUNKS * 16;
+    static_assert(NT == 256, "256 threads per CTA");
+
+    __device__ static __forceinline__ int sw(int r, int kq) {
+        return r * CPR + (kq ^ ((r >> SWS) & (SWB - 1)));
+    }
+};
+
+// Processes one work unit with tile shape <TR_T, TC_T, MC, KC, STAGES>.
+template <int TR_T, int TC_T, int MC, int KC, int STAGES>
+__device__ __forceinline__ void process_unit(uint4 *smem, const InstView &V, const WorkUnit &wu) {
+    using T = Tile<TR_T, TC_T, MC, KC, STAGES>;
+    const int tid = threadIdx.x;
+    const int tc = tid % TC_T;
+    const int tr = tid / TC_T;
+    const uint32_t nst = wu.klen / KC;
+
+    auto fill = [&](uint32_t stage, int buf) {
+        uint4 *rows = smem + (size_t)buf * T::STAGE_CHUNKS;
+        uint4 *cols = rows + T::ROW_CHUNKS;
+        const uint32_t kbase = wu.k0 + stage * KC;
+        for (int q = tid; q < T::ROW_CHUNKS; q += T::NT) {
+            const int r = q / T::CPR, kq = q % T::CPR;
+            const uint32_t g = wu.r0 + r;
+            const bool ok = g < wu.r1;
+            const uint4 *src = V.bm;
+            if (ok) {
+                uint32_t w = wrap_word(kbase + 4u * kq, __ldg(&V.wshift[g]));
+                src = V.bm + (size_t)__ldg(&V.line_off[g]) * 8u + (w >> 2);
+            }
+            cp_async16(smem_u32(rows + T::sw(r, kq)), src, ok);
+        }
+        for (int q = tid; q < T::COL_CHUNKS; q += T::NT) {
+            const int c = q / T::CPR, kq = q % T::CPR;
+            const uint32_t g = wu.c0 + c;
+            const bool ok = g < wu.c1;
+            const uint4 *src = V.bm;
+            if (ok) src = V.bm + (size_t)__ldg(&V.line_off[g]) * 8u + ((kbase >> 2) + kq);
+            cp_async16(smem_u32(cols + T::sw(c, kq)), src, ok);
+        }
+    };
+
+    uint32_t acc[8][MC];
+#pragma unroll
+    for (int a = 0; a < 8; a++)
+#pragma unroll
+        for (int b = 0; b < MC; b++) acc[a][b] = 0;
+
+#pragma unroll
+    for (int s = 0; s < STAGES - 1; s++) {
+        if ((uint32_t)s < nst) fill(s, s);
+        cp_async_commit();
+    }
+    for (uint32_t s = 0; s < nst; s++) {
+        cp_async_wait<STAGES - 2>();
+        __syncthreads();
+        {
+            uint32_t nxt = s + STAGES - 1;
+            if (nxt < nst) fill(nxt, nxt % STAGES);
+            cp_async_commit();
+        }
+        const uint4 *rows = smem + (size_t)(s % STAGES) * T::STAGE_CHUNKS;
+        const uint4 *cols = rows + T::ROW_CHUNKS;
+#pragma unroll 1
+        for (int kq = 0; kq < T::CPR; kq++) {
+            uint4 X[8], Y[MC];
+#pragma unroll
+            for (int a = 0; a < 8; a++) X[a] = rows[T::sw(tr + TR_T * a, kq)];
+#pragma unroll
+            for (int b = 0; b < MC; b++) Y[b] = cols[T::sw(tc + TC_T * b, kq)];
+#pragma unroll
+            for (int kk = 0; kk < 4; kk++) {
+                uint32_t yw[MC], yi[MC];
+#pragma unroll
+                for (int b = 0; b < MC; b++) {
+                    yw[b] = lane_word(Y[b], kk);
+                    yi[b] = yw[b] & 0x80808080u;
+                }
+#pragma unroll
+                for (int a = 0; a < 8; a++) {
+                    const uint32_t xw = lane_word(X[a], kk);
+                    const uint32_t xi = xw & 0x80808080u;
+#pragma unroll
+                    for (int b = 0; b < MC; b++) acc[a][b] = swar_step(acc[a][b], xw, xi, yw[b], yi[b]);
+                }
+            }
+        }
+    }
+    cp_async_wait<0>();
+    __syncthreads();
+
+    // epilogue: partial supports into the packed upper triangle (original ids)
+    const uint64_t n = V.n;
+#pragma unroll
+    for (int a = 0; a < 8; a++) {
+        const uint32_t gi = wu.r0 + tr + TR_T * a;
+        if (gi >= wu.r1) continue;
+        const uint32_t oi = __ldg(&V.order[gi]);
+#pragma unroll
+        for (int b = 0; b < MC; b++) {
+            const uint32_t gj = wu.c0 + tc + TC_T * b;
+            const uint32_t v = acc[a][b] >> 7;
+            if (gj < wu.c1 && gi < gj && v) {
+                const uint32_t oj = __ldg(&V.order[gj]);
+                const uint64_t lo = oi < oj ? oi : oj, hi = oi < oj ? oj : oi;
+                atomicAdd(&V.C[lo * n - lo * (lo + 1) / 2 + (hi - lo - 1)], v);
+            }
+        }
+    }
+}
+
+#define BM_SHAPE_LIST(X)          \
+    X(0, 16, 16, 8, 32, 3)        \
+    X(1, 32, 8, 8, 32, 3)         \
+    X(2, 64, 4, 8, 32, 2)         \
+    X(3, 128, 2, 8, 16, 2)        \
+    X(4, 256, 1, 8, 8, 2)         \
+    X(5, 256, 1, 4, 8, 2)
+
+size_t compare_smem_bytes(uint32_t shape_idx) {
+#define X(i, a, b, c, d, e) if (shape_idx == i) return Tile<a, b, c, d, e>::SMEM;
+    BM_SHAPE_LIST(X)
+#undef X
+    return 0;
+}
+
+static size_t max_smem_bytes() {
+    size_t m = 0;
+    for (uint32_t s = 0; s < NUM_SHAPES; s++) m = std::max(m, compare_smem_bytes(s));
+    return m;
+}
+
+// Persistent compare kernel: each CTA pulls units (longest first) from the
+// queue until it is empty.  Every unit names its tile shape and instance.
+__global__ void __launch_bounds__(256, 1)
+k_compare(const InstView *__restrict__ views, const WorkUnit *__restrict__ units, uint32_t count,
+          uint32_t *__restrict__ counter) {
+    extern __shared__ __align__(16) uint4 smem[];
+    __shared__ uint32_t s_unit;
+    for (;;) {
+        if (threadIdx.x == 0) s_unit = atomicAdd(counter, 1u);
+        __syncthreads();
+        const uint32_t u = s_unit;
+        __syncthreads();
+        if (u >= count) break;
+        const WorkUnit wu = units[u];
+        const InstView V = views[wu.inst];
+        switch (wu.shape) {
+#define X(i, a, b, c, d, e) case i: process_unit<a, b, c, d, e>(smem, V, wu); break;
+            BM_SHAPE_LIST(X)
+#undef X
+            default: break;
+        }
+    }
+}
+
+static size_t g_compare_smem = 0;
+
+void prepare_compare() {
+    if (!g_compare_smem) {
+        size_t smem = max_smem_bytes();
+        BM_CUDA(cudaFuncSetAttribute(k_compare, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        g_compare_smem = smem;
+    }
+}
+
+void launch_compare(const InstView *d_views, const WorkUnit *d_units, uint32_t count, uint32_t *d_counter,
+                    uint32_t grid, cudaStream_t st) {
+    if (!count) return;
+    prepare_compare();
+    k_compare<<<grid, 256, g_compare_smem, st>>>(d_views, d_units, count, d_counter);
+    BM_CHECK_LAUNCH();
+}
+
+// ---- schedule ------------------------------------------------------------------
+
+// Width in words of sorted item q.
+static inline uint64_t words_of(const batmap_set *S, uint32_t q) {
+    return 3ull << S->wshift_sorted[q];
+}
+
+struct Tile2 {
+    uint32_t r0, r1, c0, c1;
+};
+
+static void class_tiles(uint32_t cb, uint32_t ce, const ShapeDesc &sh, std::vector<Tile2> *out) {
+    for (uint32_t c0 = cb; c0 < ce; c0 += sh.TC) {
+        uint32_t c1 = std::min(ce, c0 + sh.TC);
+        uint32_t rows = c1 - 1;  // rows [0, c1 - 1) pair with some column of the block
+        for (uint32_t r0 = 0; r0 < rows; r0 += sh.TR) out->push_back({r0, std::min(rows, r0 + sh.TR), c0, c1});
+    }
+}
+
+void schedule_units(const batmap_set *S, uint32_t force_shape, const double *shape_eff,
+                    double target_cost, std::vector<WorkUnit> *out) {
+    const uint32_t ncls = (uint32_t)S->class_begin.size() - 1;
+    struct Pick {
+        uint32_t shape;
+        std::vector<Tile2> tiles;
+        uint64_t K;
+    };
+    std::vector<Pick> picks;
+    double total = 0.0;
+    for (uint32_t c = 0; c < ncls; c++) {
+        uint32_t cb = S->class_begin[c], ce = S->class_begin[c + 1];
+        uint64_t K = words_of(S, cb);
+        Pick best{0, {}, K};
+        double best_cost = INFINITY;
+        for (uint32_t s = 0; s < (uint32_t)NUM_SHAPES; s++) {
+            if (force_shape && s + 1 != force_shape) continue;
+            if (K % SHAPES[s].KC) continue;
+            std::vector<Tile2> tiles;
+            class_tiles(cb, ce, SHAPES[s], &tiles);
+            double cost = (double)tiles.size() * SHAPES[s].TR * SHAPES[s].TC * (double)K /
+                          (shape_eff ? shape_eff[s] : SHAPES[s].eff);
+            if (cost < best_cost) {
+                best_cost = cost;
+                best = Pick{s, std::move(tiles), K};
+            }
+        }
+        if (!best.tiles.empty()) {
+            total += best_cost;
+            picks.push_back(std::move(best));
+        }
+    }
+    if (target_cost <= 0.0) target_cost = total / (8.0 * device_sms());
+    for (auto &p : picks) {
+        const ShapeDesc &sh = SHAPES[p.shape];
+        const double tile_cost = (double)sh.TR * sh.TC * (double)p.K;
+        uint64_t nk = (uint64_t)std::ceil(tile_cost / std::max(target_cost, 1.0));
+        nk = std::max<uint64_t>(1, std::min<uint64_t>(nk, p.K / sh.KC));
+        uint64_t klen = (p.K + nk - 1) / nk;
+        klen = (klen + sh.KC - 1) / sh.KC * sh.KC;
+        klen = std::min<uint64_t>(klen, 1ull << 22);  // 128 * 4 * klen < 2^32
+        for (const Tile2 &t : p.tiles)
+            for (uint64_t k0 = 0; k0 < p.K; k0 += klen)
+                out->push_back({t.r0, t.r1, t.c0, t.c1, (uint32_t)k0,
+                                (uint32_t)std::min<uint64_t>(klen, p.K - k0), 0, p.shape});
+    }
+    sort_units(out);
+}
+
+double unit_cost(const WorkUnit &u) {
+    return (double)SHAPES[u.shape].TR * SHAPES[u.shape].TC * (double)u.klen / SHAPES[u.shape].eff;
+}
+
+void sort_units(std::vector<WorkUnit> *units) {
+    std::stable_sort(units->begin(), units->end(),
+                     [](const WorkUnit &a, const WorkUnit &b) { return unit_cost(a) > unit_cost(b); });
+}
+
+void build_schedule(batmap_set *S) {
+    S->units.clear();
+    schedule_units(S, S->params.tile, nullptr, 0.0, &S->units);
+    S->d_units.alloc(S->units.size());
+    if (!S->units.empty())
+        BM_CUDA(cudaMemcpyAsync(S->d_units.p, S->units.data(), S->units.size() * sizeof(WorkUnit),
+                                cudaMemcpyHostToDevice, S->stream));
+}
+
+}  // namespace bm

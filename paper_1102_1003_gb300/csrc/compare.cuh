@@ -1,0 +1,49 @@
+// All-pairs BatMap comparison (the hot loop of Sec. III-B): tile shapes,
+// schedule construction and launch.
+#pragma once
+
+#include "common.cuh"
+
+namespace bm {
+
+// Tile shapes of the compare kernel.  A CTA of 256 threads owns a tile of
+// TR rows x TC columns (each thread 8 rows x MC columns) and streams the
+// column width in stages of KC words through shared memory.
+struct ShapeDesc {
+    uint32_t id;   // 1-based; 0 = automatic
+    uint32_t TR, TC, MC, KC, stages;
+    double eff;    // relative throughput per padded word-pair (scheduler prior)
+};
+
+constexpr int NUM_SHAPES = 6;
+extern const ShapeDesc SHAPES[NUM_SHAPES];
+
+// Number of SMs of the current device (cached).
+int device_sms();
+
+// Build the compare work units of one set (fills S->units, longest first,
+// and uploads them).  `shape_eff` (NULL = built-in prior) gives the relative
+// throughput of each shape (autotuner); `force_shape` (1..NUM_SHAPES) pins
+// one shape; target_cost <= 0 picks about 8 units per SM.
+void build_schedule(batmap_set *S);
+void schedule_units(const batmap_set *S, uint32_t force_shape, const double *shape_eff,
+                    double target_cost, std::vector<WorkUnit> *out);
+
+// Estimated cost of a unit (padded word-pairs / shape efficiency) and the
+// longest-first order used by every launch.
+double unit_cost(const WorkUnit &u);
+void sort_units(std::vector<WorkUnit> *units);
+
+// Launch the persistent compare kernel over `count` units at d_units (any
+// mix of shapes and instances), pulling work from d_counter (zeroed by the
+// caller).  One CTA per SM.
+void launch_compare(const InstView *d_views, const WorkUnit *d_units, uint32_t count,
+                    uint32_t *d_counter, uint32_t grid, cudaStream_t st);
+
+// Sets the kernel's shared-memory attribute (call before stream capture).
+void prepare_compare();
+
+// Shared-memory bytes of one shape (for occupancy and launch).
+size_t compare_smem_bytes(uint32_t shape_idx);
+
+}  // namespace bm

@@ -1,0 +1,73 @@
+"""The C-ABI library loads and exports every entry point include/batmap.h declares
+(CPU only: no compute call is made)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if not h.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", h)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*([A-Za-z_][A-Za-z0-9_]*)\s*\(",
+                             text, flags=re.M):
+            names.append(m.group(1))
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__ as g
+    g.build()
+    from paper_1102_1003_gb300 import batmap
+    return ctypes.CDLL(batmap.LIB_PATH)
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("batmap_build", "pair_support_all", "pair_support_batch", "batmap_free",
+                     "batmap_last_error", "pair_support_host"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in _declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_names_match_header():
+    from paper_1102_1003_gb300 import batmap
+    assert set(batmap.EXPORTED) <= set(_declared_functions())
+    for name in batmap.EXPORTED:
+        if name not in ("batmap_last_error",):
+            assert hasattr(batmap, name) or name.startswith("batmap_"), name
+
+
+def test_default_params_without_gpu(lib):
+    from paper_1102_1003_gb300 import batmap
+    p = batmap.batmap_default_params()
+    assert (p.load_num, p.load_den, p.max_loop, p.min_shift, p.tile, p.validate) == (2, 1, 32, 7, 0, 1)
+    assert batmap.load_library().batmap_last_error() == b""
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    from paper_1102_1003_gb300 import batmap
+    with pytest.raises(ImportError):
+        batmap.load_library.__wrapped__(str(tmp_path / "nope.so")) if hasattr(
+            batmap.load_library, "__wrapped__") else _load_missing(batmap, tmp_path)
+
+
+def _load_missing(batmap, tmp_path):
+    saved = batmap._lib
+    batmap._lib = None
+    try:
+        batmap.load_library(str(tmp_path / "libbatmap_missing.so"))
+    finally:
+        batmap._lib = saved
