@@ -58,10 +58,12 @@ typedef int batmap_status;
  *       Must be >= 7 so that every BatMap is a multiple of 384 bytes.
  *       Default 7.
  *   tile : 0 lets the scheduler choose compare tile shapes per width class;
- *       1..6 forces one shape for every class (testing and autotuning).
+ *       1..12 forces one shape for every class (testing and autotuning).
  *   validate : nonzero checks that tids are strictly increasing and < m per
  *       item and that each permutation row is a bijection of [0, m); a
  *       violation returns BATMAP_ERR_ARG.  Default 1.
+ *   shape_mask : bit s-1 allows compare tile shape s (1..12) when tile is 0;
+ *       0 allows every shape.  Default 0.
  */
 typedef struct batmap_params {
     uint32_t load_num;
@@ -70,6 +72,7 @@ typedef struct batmap_params {
     uint32_t min_shift;
     uint32_t tile;
     uint32_t validate;
+    uint32_t shape_mask;
 } batmap_params;
 
 /* Opaque handle to n BatMaps built from one instance (owned by the library). */

@@ -33,7 +33,8 @@ EXPORTED = [
 class batmap_params(ctypes.Structure):
     _fields_ = [("load_num", ctypes.c_uint32), ("load_den", ctypes.c_uint32),
                 ("max_loop", ctypes.c_uint32), ("min_shift", ctypes.c_uint32),
-                ("tile", ctypes.c_uint32), ("validate", ctypes.c_uint32)]
+                ("tile", ctypes.c_uint32), ("validate", ctypes.c_uint32),
+                ("shape_mask", ctypes.c_uint32)]
 
 
 class batmap_info(ctypes.Structure):

@@ -353,6 +353,8 @@ void build_set(batmap_set *S, const uint64_t *d_offsets, const uint32_t *d_tids,
     }
     S->class_begin.push_back(n);
     S->bytes = pos;
+    // the compare kernel addresses BatMaps as 32-bit indices of 16-byte chunks
+    BM_REQUIRE(pos <= (1ull << 36), BATMAP_ERR_ARG, "BatMaps of one set exceed 64 GB; split the instance");
 
     // algorithmic work of the compare: sum over pairs of the wider width / 4
     double wp = 0.0;

@@ -8,7 +8,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/batmap.h"
+#include "batmap.h"
 
 namespace bm {
 

@@ -31,13 +31,17 @@
 
 namespace bm {
 
+// Shapes 1..6 stage tiles through shared memory (cp.async ring); shapes
+// 7..12 stream operands from global memory into registers.  The efficiency
+// column is the prior relative throughput per padded word pair used when no
+// autotuned table is available.
 const ShapeDesc SHAPES[NUM_SHAPES] = {
-    {1, 128, 128, 8, 32, 3, 1.00},
-    {2, 256, 64, 8, 32, 3, 0.98},
-    {3, 512, 32, 8, 32, 2, 0.95},
-    {4, 1024, 16, 8, 16, 2, 0.92},
-    {5, 2048, 8, 8, 8, 2, 0.88},
-    {6, 2048, 4, 4, 8, 2, 0.80},
+    {1, 128, 128, 8, 32, 3, 1.00},  {2, 256, 64, 8, 32, 3, 0.96},
+    {3, 512, 32, 8, 32, 2, 0.70},   {4, 1024, 16, 8, 16, 2, 0.55},
+    {5, 2048, 8, 8, 8, 2, 0.40},    {6, 2048, 4, 4, 8, 2, 0.30},
+    {7, 128, 128, 8, 4, 0, 0.90},   {8, 256, 64, 8, 4, 0, 0.90},
+    {9, 512, 32, 8, 4, 0, 0.88},    {10, 1024, 16, 8, 4, 0, 0.86},
+    {11, 2048, 8, 8, 4, 0, 0.84},   {12, 2048, 4, 4, 4, 0, 0.70},
 };
 
 int device_sms() {
@@ -73,13 +77,17 @@ __device__ __forceinline__ uint32_t lane_word(const uint4 &v, int kk) {
     return kk == 0 ? v.x : kk == 1 ? v.y : kk == 2 ? v.z : v.w;
 }
 
-// One 32-bit word pair: adds 128 per counted slot to acc.
+// One 32-bit word pair: adds 128 per counted slot to acc.  Written as
+// explicit three-input logic operations (lop3) so that each boolean step is
+// one instruction: LUT 0x28 = (a ^ b) & c, LUT 0x0E = ~a & (b | c).
 __device__ __forceinline__ uint32_t swar_step(uint32_t acc, uint32_t x, uint32_t xi, uint32_t y,
                                               uint32_t yi) {
-    uint32_t l = (x ^ y) & 0x7F7F7F7Fu;
-    uint32_t t = l + 0x7F7F7F7Fu;
-    uint32_t q = ~t & (xi | yi);
-    return __dp4a(q, 0x01010101u, acc);
+    uint32_t l, t, q;
+    asm("lop3.b32 %0, %1, %2, 0x7F7F7F7F, 0x28;" : "=r"(l) : "r"(x), "r"(y));
+    asm("add.u32 %0, %1, 0x7F7F7F7F;" : "=r"(t) : "r"(l));
+    asm("lop3.b32 %0, %1, %2, %3, 0x0E;" : "=r"(q) : "r"(t), "r"(xi), "r"(yi));
+    asm("dp4a.u32.u32 %0, %1, 0x01010101, %0;" : "+r"(acc) : "r"(q));
+    return acc;
 }
 
 template <int TR_T, int TC_T, int MC, int KC, int STAGES>
@@ -205,6 +213,113 @@ __device__ __forceinline__ void process_unit(uint4 *smem, const InstView &V, con
     }
 }
 
+// Register-streaming variant: every thread loads its own 8 row words and MC
+// column words per 4-word step straight from global memory (128-bit loads
+// through L1; lanes of a warp that share a row or a column are served by one
+// request) and prefetches the next step while comparing the current one.
+// No shared memory and no barrier: suited to narrow column tiles, where a
+// loaded row word has only a few partners and staging costs more than it
+// saves.  The wrap of a narrower row is an incremental index reset.
+template <int TR_T, int TC_T, int MC>
+__device__ __forceinline__ void process_unit_direct(const InstView &V, const WorkUnit &wu) {
+    const int tid = threadIdx.x;
+    const int tc = tid % TC_T;
+    const int tr = tid / TC_T;
+    const uint32_t q0 = wu.k0 >> 2;  // first 16-byte chunk of the column range
+    const uint32_t nq = wu.klen >> 2;
+    const uint4 zero = make_uint4(0, 0, 0, 0);
+    const uint4 *__restrict__ bm = V.bm;
+
+    // row state: chunk index of the row start, current chunk, row length (chunks)
+    uint32_t rbase[8], rcur[8], rlen[8];
+#pragma unroll
+    for (int a = 0; a < 8; a++) {
+        const uint32_t g = wu.r0 + tr + TR_T * a;
+        if (g < wu.r1) {
+            const uint32_t e = __ldg(&V.wshift[g]);
+            rbase[a] = __ldg(&V.line_off[g]) * 8u;
+            rlen[a] = 3u << (e - 2);
+            rcur[a] = wrap_word(wu.k0, e) >> 2;
+        } else {
+            rbase[a] = 0xFFFFFFFFu;  // marks an empty row slot
+            rlen[a] = 1;
+            rcur[a] = 0;
+        }
+    }
+    uint32_t cbase[MC];
+#pragma unroll
+    for (int b = 0; b < MC; b++) {
+        const uint32_t g = wu.c0 + tc + TC_T * b;
+        cbase[b] = g < wu.c1 ? __ldg(&V.line_off[g]) * 8u + q0 : 0xFFFFFFFFu;
+    }
+
+    uint32_t acc[8][MC];
+#pragma unroll
+    for (int a = 0; a < 8; a++)
+#pragma unroll
+        for (int b = 0; b < MC; b++) acc[a][b] = 0;
+
+    auto load_rows = [&](uint4 (&X)[8]) {
+#pragma unroll
+        for (int a = 0; a < 8; a++) {
+            X[a] = rbase[a] != 0xFFFFFFFFu ? __ldg(bm + (size_t)rbase[a] + rcur[a]) : zero;
+            rcur[a] = (rcur[a] + 1 == rlen[a]) ? 0 : rcur[a] + 1;
+        }
+    };
+
+    uint4 X[8];
+    load_rows(X);
+#pragma unroll 1
+    for (uint32_t q = 0; q < nq; q++) {
+        uint4 Y[MC];
+#pragma unroll
+        for (int b = 0; b < MC; b++) Y[b] = cbase[b] != 0xFFFFFFFFu ? __ldg(bm + (size_t)cbase[b] + q) : zero;
+        uint4 Xn[8];
+        if (q + 1 < nq) {
+            load_rows(Xn);
+        } else {
+#pragma unroll
+            for (int a = 0; a < 8; a++) Xn[a] = zero;
+        }
+#pragma unroll
+        for (int kk = 0; kk < 4; kk++) {
+            uint32_t yw[MC], yi[MC];
+#pragma unroll
+            for (int b = 0; b < MC; b++) {
+                yw[b] = lane_word(Y[b], kk);
+                yi[b] = yw[b] & 0x80808080u;
+            }
+#pragma unroll
+            for (int a = 0; a < 8; a++) {
+                const uint32_t xw = lane_word(X[a], kk);
+                const uint32_t xi = xw & 0x80808080u;
+#pragma unroll
+                for (int b = 0; b < MC; b++) acc[a][b] = swar_step(acc[a][b], xw, xi, yw[b], yi[b]);
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < 8; a++) X[a] = Xn[a];
+    }
+
+    const uint64_t n = V.n;
+#pragma unroll
+    for (int a = 0; a < 8; a++) {
+        const uint32_t gi = wu.r0 + tr + TR_T * a;
+        if (gi >= wu.r1) continue;
+        const uint32_t oi = __ldg(&V.order[gi]);
+#pragma unroll
+        for (int b = 0; b < MC; b++) {
+            const uint32_t gj = wu.c0 + tc + TC_T * b;
+            const uint32_t v = acc[a][b] >> 7;
+            if (gj < wu.c1 && gi < gj && v) {
+                const uint32_t oj = __ldg(&V.order[gj]);
+                const uint64_t lo = oi < oj ? oi : oj, hi = oi < oj ? oj : oi;
+                atomicAdd(&V.C[lo * n - lo * (lo + 1) / 2 + (hi - lo - 1)], v);
+            }
+        }
+    }
+}
+
 #define BM_SHAPE_LIST(X)          \
     X(0, 16, 16, 8, 32, 3)        \
     X(1, 32, 8, 8, 32, 3)         \
@@ -212,6 +327,14 @@ __device__ __forceinline__ void process_unit(uint4 *smem, const InstView &V, con
     X(3, 128, 2, 8, 16, 2)        \
     X(4, 256, 1, 8, 8, 2)         \
     X(5, 256, 1, 4, 8, 2)
+
+#define BM_DIRECT_LIST(X) \
+    X(6, 16, 16, 8)         \
+    X(7, 32, 8, 8)          \
+    X(8, 64, 4, 8)          \
+    X(9, 128, 2, 8)         \
+    X(10, 256, 1, 8)        \
+    X(11, 256, 1, 4)
 
 size_t compare_smem_bytes(uint32_t shape_idx) {
 #define X(i, a, b, c, d, e) if (shape_idx == i) return Tile<a, b, c, d, e>::SMEM;
@@ -244,6 +367,9 @@ k_compare(const InstView *__restrict__ views, const WorkUnit *__restrict__ units
         switch (wu.shape) {
 #define X(i, a, b, c, d, e) case i: process_unit<a, b, c, d, e>(smem, V, wu); break;
             BM_SHAPE_LIST(X)
+#undef X
+#define X(i, a, b, c) case i: process_unit_direct<a, b, c>(V, wu); break;
+            BM_DIRECT_LIST(X)
 #undef X
             default: break;
         }
@@ -304,6 +430,7 @@ void schedule_units(const batmap_set *S, uint32_t force_shape, const double *sha
         double best_cost = INFINITY;
         for (uint32_t s = 0; s < (uint32_t)NUM_SHAPES; s++) {
             if (force_shape && s + 1 != force_shape) continue;
+            if (!force_shape && S->params.shape_mask && !((S->params.shape_mask >> s) & 1u)) continue;
             if (K % SHAPES[s].KC) continue;
             std::vector<Tile2> tiles;
             class_tiles(cb, ce, SHAPES[s], &tiles);

@@ -7,15 +7,16 @@
 namespace bm {
 
 // Tile shapes of the compare kernel.  A CTA of 256 threads owns a tile of
-// TR rows x TC columns (each thread 8 rows x MC columns) and streams the
-// column width in stages of KC words through shared memory.
+// TR rows x TC columns (each thread 8 rows x MC columns).  Staged shapes
+// (stages > 0) stream the column width in stages of KC words through shared
+// memory; direct shapes (stages == 0) stream 4-word steps into registers.
 struct ShapeDesc {
     uint32_t id;   // 1-based; 0 = automatic
     uint32_t TR, TC, MC, KC, stages;
     double eff;    // relative throughput per padded word-pair (scheduler prior)
 };
 
-constexpr int NUM_SHAPES = 6;
+constexpr int NUM_SHAPES = 12;
 extern const ShapeDesc SHAPES[NUM_SHAPES];
 
 // Number of SMs of the current device (cached).

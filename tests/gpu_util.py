@@ -28,8 +28,9 @@ def run_all_pairs(inst, s=None, perm_seed=0, params=None, want_full=True):
     return f, n_out, pairs.cpu().numpy().astype(np.uint32).reshape(-1, 3), bset
 
 
-def layout_errors(inst, bset, perm_seed):
-    """Check every item's BatMap against the definition; returns a list of errors."""
+def layout_errors(inst, bset, perm_seed, c_num=2, c_den=1):
+    """Check every item's BatMap against the definition (hash ranges from the
+    load factor c = c_num / c_den); returns a list of errors."""
     import paper_1102_1003_gb300 as pkg
     from oracle import batmap_rules as R
     lay = pkg.batmap_export_layout(bset)
@@ -44,8 +45,8 @@ def layout_errors(inst, bset, perm_seed):
     for i in range(inst.n):
         r = int(lay["range"][i])
         size = len(inst.tidlist(i))
-        if r != R.hash_range(size, r0):
-            errs.append(f"item {i}: r={r} but the rule gives {R.hash_range(size, r0)}")
+        if r != R.hash_range(size, r0, c_num, c_den):
+            errs.append(f"item {i}: r={r} but the rule gives {R.hash_range(size, r0, c_num, c_den)}")
             continue
         b0 = int(lay["byte_offset"][i])
         bm = lay["bytes"][b0:b0 + 3 * r]

@@ -53,7 +53,8 @@ def test_binding_names_match_header():
 def test_default_params_without_gpu(lib):
     from paper_1102_1003_gb300 import batmap
     p = batmap.batmap_default_params()
-    assert (p.load_num, p.load_den, p.max_loop, p.min_shift, p.tile, p.validate) == (2, 1, 32, 7, 0, 1)
+    assert (p.load_num, p.load_den, p.max_loop, p.min_shift, p.tile, p.validate, p.shape_mask) == \
+        (2, 1, 32, 7, 0, 1, 0)
     assert batmap.load_library().batmap_last_error() == b""
 
 

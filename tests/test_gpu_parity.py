@@ -65,7 +65,7 @@ def test_zipf_mixed_widths_exact_and_valid(seed):
     assert layout_errors(inst, bset, seed) == []
 
 
-@pytest.mark.parametrize("tile", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("tile", list(range(1, 13)))
 def test_every_tile_shape_exact(tile):
     import paper_1102_1003_gb300 as pkg
     inst = datagen.zipf_tidlists(40_000, 333, 0.04, seed=7, s=30)
@@ -83,7 +83,7 @@ def test_forced_failures_stay_exact(params):
     info = bset.info
     assert info["n_failed"] > 0 and info["n_corrections"] > 0
     _check_exact(inst, full, n_out, pairs)
-    assert layout_errors(inst, bset, 3) == []
+    assert layout_errors(inst, bset, 3, params.get("load_num", 2), params.get("load_den", 1)) == []
 
 
 def test_all_elements_of_an_item_fail():
