@@ -222,6 +222,34 @@ typedef struct batmap_out {
 batmap_status pair_support_batch(batmap_set *const *sets, const uint32_t *s, uint32_t k,
                                  batmap_out *outs, cudaStream_t stream);
 
+/*
+ * Frequent pairs from already counted supports, for callers that cannot
+ * allocate device memory.  The paper has no counterpart: this is an
+ * interface convenience.
+ *
+ * Callers such as a serving loop confined to a fixed, pre-partitioned memory
+ * budget, or latency-critical code that must not pay for the implicit device
+ * synchronisation cudaMalloc / cudaFree may perform, cannot let the library
+ * allocate.  This call performs the same support-threshold compaction as
+ * pair_support_all and allocates nothing: its scratch is a fixed device array
+ * of 512 KiB + 8 bytes inside the library, which every GPU that loads the
+ * library holds until the process exits.
+ *   d_full  : device uint32[n(n-1)/2], supports of all pairs i < j as the
+ *             packed upper triangle written by pair_support_all's d_full.
+ *   n       : items; at most 23,170 (n(n-1)/2 <= 2^28).  Larger n returns
+ *             BATMAP_ERR_CAPACITY without touching the GPU.
+ *   s       : support threshold.
+ *   d_pairs, cap, n_out : as in pair_support_all (lexicographic triples;
+ *             BATMAP_ERR_CAPACITY with the first cap triples if cap is short).
+ * The first call on a device looks up the device address of the fixed array
+ * (once per device, with that device current); make that first call before
+ * any stream capture.  All calls share the one array: calls whose work
+ * overlaps on the GPU (different streams or threads without ordering) race
+ * and must not be issued.  Synchronises the stream.
+ */
+batmap_status pair_threshold_noalloc(const uint32_t *d_full, uint32_t n, uint32_t s, uint32_t *d_pairs,
+                                     uint64_t cap, uint64_t *n_out, cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

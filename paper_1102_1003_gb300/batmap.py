@@ -26,7 +26,7 @@ BATMAP_ERR_INTERNAL = -6
 EXPORTED = [
     "batmap_default_params", "batmap_last_error", "batmap_build", "batmap_free",
     "batmap_get_info", "batmap_export_layout", "pair_support_all", "pair_support_host",
-    "pair_support_batch", "batmap_get_timing", "batmap_kernel_launches",
+    "pair_support_batch", "batmap_get_timing", "batmap_kernel_launches", "pair_threshold_noalloc",
 ]
 
 
@@ -107,6 +107,8 @@ def load_library(path: str = LIB_PATH):
     L.batmap_get_timing.restype = ctypes.c_int
     L.batmap_kernel_launches.argtypes = []
     L.batmap_kernel_launches.restype = u64
+    L.pair_threshold_noalloc.argtypes = [vp, u32, u32, vp, u64, ctypes.POINTER(u64), vp]
+    L.pair_threshold_noalloc.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -253,5 +255,18 @@ def pair_support_host(m: int, offsets: np.ndarray, tids: np.ndarray, perm: np.nd
     rc = L.pair_support_host(pp, int(m), n, offsets.ctypes.data, tids.ctypes.data if tids.size else None,
                              perm.ctypes.data, int(s), pairs_out.ctypes.data, pairs_out.size // 3,
                              ctypes.byref(n_out), _stream_handle(stream))
+    _check(rc, allow=(BATMAP_ERR_CAPACITY,))
+    return int(n_out.value)
+
+
+def pair_threshold_noalloc(full, n: int, s: int, pairs, stream=None) -> int:
+    """Frequent pairs from the packed supports `full` into the caller's `pairs`
+    buffer (cuda int32 [cap, 3]) without any device allocation by the library;
+    returns n_out.  For callers that cannot allocate device memory."""
+    L = load_library()
+    n_out = ctypes.c_uint64(0)
+    cap = pairs.numel() // 3 if pairs is not None else 0
+    rc = L.pair_threshold_noalloc(_ptr(full), int(n), int(s), _ptr(pairs), cap, ctypes.byref(n_out),
+                                  _stream_handle(stream))
     _check(rc, allow=(BATMAP_ERR_CAPACITY,))
     return int(n_out.value)
