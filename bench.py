@@ -172,6 +172,44 @@ def run_reference(args, inst, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def dense_leg(args, inst, off, tids, n_out_ref, peaks, peak_kind):
+    """The dense-bitmap tensor-core comparison path on the same workload."""
+    import torch
+    import paper_1102_1003_gb300 as pkg
+    npairs = inst.n * (inst.n - 1) // 2
+    pairs = torch.empty((max(n_out_ref, 1), 3), dtype=torch.int32, device=off.device)
+    for _ in range(args.warmup):
+        pkg.pair_support_dense(inst.m, off, tids, inst.s, pairs=pairs)
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    gemm, build = [], []
+    ev0.record(stream)
+    for _ in range(args.steps):
+        k, _, t = pkg.pair_support_dense(inst.m, off, tids, inst.s, pairs=pairs)
+        gemm.append(t["compare_ms"])
+        build.append(t["build_ms"])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    assert k == n_out_ref, (k, n_out_ref)
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    # tensor work actually issued: upper-triangle tiles of 128 x 256 over the padded K
+    n, bm, bn = inst.n, 128, 256
+    tiles = sum(min((n + bm - 1) // bm, 2 * bj + 2) for bj in range((n + bn - 1) // bn))
+    kpad = (inst.m + 63) // 64 * 64
+    flops_issued = 2.0 * tiles * bm * bn * kpad
+    flops_alg = 2.0 * npairs * inst.m
+    g = statistics.mean(gemm) / 1e3
+    peak = peaks.get("bf16_tflops", 1900.0)
+    return {"value": npairs * args.steps / elapsed, "unit": UNIT, "ms_per_step": 1e3 * elapsed / args.steps,
+            "phases_ms": {"bitmap": statistics.mean(build), "tensor_kernel": statistics.mean(gemm)},
+            "roofline": {"bound": "tensor", "achieved": flops_issued / g / 1e12, "peak": peak, "unit": "TFLOP/s",
+                         "frac": flops_issued / g / 1e12 / peak, "kernel": "k_dense_mmt",
+                         "peak_kind": f"bf16 dense, {peak_kind} (burst)",
+                         "algorithmic_TFLOPs": flops_alg / g / 1e12},
+            "dtype": "bf16 {0,1} operands, fp32 accumulate (exact integers < 2^24)"}
+
+
 def run_mine(args, inst, rank, world):
     import torch
     import paper_1102_1003_gb300 as pkg
@@ -291,6 +329,8 @@ def run_mine(args, inst, rank, world):
                 "d2h_bytes_per_step": int(12 * n_out + 8)},
         "clocks": clocks,
     }
+    if not args.no_dense and inst.m <= (1 << 24):
+        line["dense"] = dense_leg(args, inst, off, tids, n_out, peaks, peak_kind)
     if world == 1 and not args.no_cpu_baseline:
         rate, cores, k, dt = cpu_oracle_rate(inst, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -310,6 +350,7 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOAD_DESC), default="cfg2")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-dense", action="store_true", help="skip the dense tensor-core comparison leg")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -27,6 +27,7 @@ EXPORTED = [
     "batmap_default_params", "batmap_last_error", "batmap_build", "batmap_free",
     "batmap_get_info", "batmap_export_layout", "pair_support_all", "pair_support_host",
     "pair_support_batch", "batmap_get_timing", "batmap_kernel_launches", "pair_threshold_noalloc",
+    "pair_support_dense",
 ]
 
 
@@ -107,6 +108,9 @@ def load_library(path: str = LIB_PATH):
     L.batmap_get_timing.restype = ctypes.c_int
     L.batmap_kernel_launches.argtypes = []
     L.batmap_kernel_launches.restype = u64
+    L.pair_support_dense.argtypes = [u32, u32, vp, vp, u32, vp, u64, ctypes.POINTER(u64), vp,
+                                     ctypes.POINTER(batmap_timing), vp]
+    L.pair_support_dense.restype = ctypes.c_int
     L.pair_threshold_noalloc.argtypes = [vp, u32, u32, vp, u64, ctypes.POINTER(u64), vp]
     L.pair_threshold_noalloc.restype = ctypes.c_int
     _lib = L
@@ -226,6 +230,27 @@ def pair_support_all(bset: BatMapSet, s: int, pairs=None, full=None, stream=None
     _check(rc, allow=(BATMAP_ERR_CAPACITY,))
     k = min(int(n_out.value), cap)
     return int(n_out.value), pairs.view(-1, 3)[:k]
+
+
+def pair_support_dense(m: int, offsets, tids, s: int, pairs=None, full=None, stream=None):
+    """Dense-bitmap tensor-core path; returns (n_out, pairs view, timing dict)."""
+    import torch
+    L = load_library()
+    n = int(offsets.numel()) - 1
+    n_out = ctypes.c_uint64(0)
+    t = batmap_timing()
+    st = _stream_handle(stream)
+    if pairs is None:
+        rc = L.pair_support_dense(int(m), n, _ptr(offsets), _ptr(tids), int(s), None, 0, ctypes.byref(n_out),
+                                  _ptr(full), ctypes.byref(t), st)
+        _check(rc, allow=(BATMAP_ERR_CAPACITY,))
+        pairs = torch.empty((max(int(n_out.value), 1), 3), dtype=torch.int32, device="cuda")
+    cap = pairs.numel() // 3
+    rc = L.pair_support_dense(int(m), n, _ptr(offsets), _ptr(tids), int(s), _ptr(pairs), cap,
+                              ctypes.byref(n_out), _ptr(full), ctypes.byref(t), st)
+    _check(rc, allow=(BATMAP_ERR_CAPACITY,))
+    k = min(int(n_out.value), cap)
+    return int(n_out.value), pairs.view(-1, 3)[:k], t.as_dict()
 
 
 def pair_support_batch(sets, s_list, pairs_list, full_list=None, stream=None):
