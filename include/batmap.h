@@ -222,6 +222,65 @@ typedef struct batmap_out {
 batmap_status pair_support_batch(batmap_set *const *sets, const uint32_t *s, uint32_t k,
                                  batmap_out *outs, cudaStream_t stream);
 
+/* ---- serving: a resident pool of sets and conjunctive queries ----------- */
+
+/* Opaque handle to a device-resident pool of sets (owned by the library). */
+typedef struct batmap_pool batmap_pool;
+
+/*
+ * Build a pool from n sets over the universe [0, m) given as CSR tidlists (as
+ * in batmap_build).  Every set keeps a device copy of its sorted tidlist; sets
+ * for which the 8-bit BatMap is compact (c |S| >= r_0, Sec. III-A) also get a
+ * BatMap built with the same GPU build as batmap_build.  The caller may free
+ * its buffers after the call.  Synchronises the stream.
+ */
+batmap_status batmap_pool_create(const batmap_params *p, uint32_t m, uint32_t n, const uint64_t *d_offsets,
+                                 const uint32_t *d_tids, const uint32_t *d_perm, cudaStream_t stream,
+                                 batmap_pool **out);
+void batmap_pool_free(batmap_pool *pool);
+/* Pool summary: BatMap-backed sets, their bytes, total elements (any may be NULL). */
+batmap_status batmap_pool_info(const batmap_pool *pool, uint32_t *n_batmaps, uint64_t *batmap_bytes,
+                               uint64_t *n_elements);
+
+/*
+ * Conjunctive queries |S_a1 cap ... cap S_ak| (Sec. I conjunctive queries;
+ * Sec. V: count, for each element of the smallest set, its occurrences in the
+ * others).  Query q names the sets h_ids[h_qoff[q] .. h_qoff[q+1]) (1..8 ids,
+ * host arrays); d_counts is a device uint64[n_queries].  Synchronises.
+ */
+batmap_status intersect_query(const batmap_pool *pool, const uint32_t *h_qoff, const uint32_t *h_ids,
+                              uint32_t n_queries, uint64_t *d_counts, cudaStream_t stream);
+
+/* Options of the serving loop. */
+typedef struct batmap_serve_opts {
+    uint32_t max_batch;   /* queries per micro-batch (default 64)                        */
+    uint32_t slots;       /* micro-batches in flight, one CUDA stream each (default 4)    */
+    uint64_t work_budget; /* admission bound on in-flight work: sum over queries of
+                             |smallest set| x sets named (default 2^26); it also sizes
+                             each slot's fixed task buffers                              */
+    uint64_t reserved;
+} batmap_serve_opts;
+
+/* Statistics of one serving run (seconds). */
+typedef struct batmap_serve_stats {
+    double makespan_s, queries_per_s, p50_s, p99_s, max_s;
+    uint64_t batches, max_inflight;
+} batmap_serve_stats;
+
+/*
+ * Continuous-batching request loop over a pool.  Query q (as in
+ * intersect_query) arrives h_arrival_s[q] seconds after the call starts
+ * (non-decreasing).  Arrived queries are admitted into a free slot while the
+ * in-flight work stays within the budget, launched as one micro-batch on the
+ * slot's stream, and overlap on the device with batches in other slots.
+ * Outputs (host): h_counts[q], h_latency_s[q] = completion - arrival, stats.
+ * opts may be NULL for the defaults.
+ */
+batmap_status batmap_serve(const batmap_pool *pool, const uint32_t *h_qoff, const uint32_t *h_ids,
+                           const double *h_arrival_s, uint32_t n_queries, const batmap_serve_opts *opts,
+                           uint64_t *h_counts, double *h_latency_s, batmap_serve_stats *stats,
+                           cudaStream_t stream);
+
 /*
  * Dense-bitmap comparison path (Sec. I-B: the bitmap vertical representation,
  * m*n bits, where a support is AND + popcount).  Builds the item x transaction

@@ -27,7 +27,8 @@ EXPORTED = [
     "batmap_default_params", "batmap_last_error", "batmap_build", "batmap_free",
     "batmap_get_info", "batmap_export_layout", "pair_support_all", "pair_support_host",
     "pair_support_batch", "batmap_get_timing", "batmap_kernel_launches", "pair_threshold_noalloc",
-    "pair_support_dense",
+    "pair_support_dense", "batmap_pool_create", "batmap_pool_free", "batmap_pool_info", "intersect_query",
+    "batmap_serve",
 ]
 
 
@@ -62,6 +63,20 @@ class batmap_timing(ctypes.Structure):
 class batmap_out(ctypes.Structure):
     _fields_ = [("d_pairs", ctypes.c_void_p), ("cap", ctypes.c_uint64),
                 ("n_out", ctypes.c_uint64), ("d_full", ctypes.c_void_p)]
+
+
+class batmap_serve_opts(ctypes.Structure):
+    _fields_ = [("max_batch", ctypes.c_uint32), ("slots", ctypes.c_uint32),
+                ("work_budget", ctypes.c_uint64), ("reserved", ctypes.c_uint64)]
+
+
+class batmap_serve_stats(ctypes.Structure):
+    _fields_ = [("makespan_s", ctypes.c_double), ("queries_per_s", ctypes.c_double),
+                ("p50_s", ctypes.c_double), ("p99_s", ctypes.c_double), ("max_s", ctypes.c_double),
+                ("batches", ctypes.c_uint64), ("max_inflight", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class BatmapError(RuntimeError):
@@ -111,6 +126,17 @@ def load_library(path: str = LIB_PATH):
     L.pair_support_dense.argtypes = [u32, u32, vp, vp, u32, vp, u64, ctypes.POINTER(u64), vp,
                                      ctypes.POINTER(batmap_timing), vp]
     L.pair_support_dense.restype = ctypes.c_int
+    L.batmap_pool_create.argtypes = [ctypes.POINTER(batmap_params), u32, u32, vp, vp, vp, vp, ctypes.POINTER(vp)]
+    L.batmap_pool_create.restype = ctypes.c_int
+    L.batmap_pool_free.argtypes = [vp]
+    L.batmap_pool_free.restype = None
+    L.batmap_pool_info.argtypes = [vp, ctypes.POINTER(u32), ctypes.POINTER(u64), ctypes.POINTER(u64)]
+    L.batmap_pool_info.restype = ctypes.c_int
+    L.intersect_query.argtypes = [vp, vp, vp, u32, vp, vp]
+    L.intersect_query.restype = ctypes.c_int
+    L.batmap_serve.argtypes = [vp, vp, vp, vp, u32, ctypes.POINTER(batmap_serve_opts), vp, vp,
+                               ctypes.POINTER(batmap_serve_stats), vp]
+    L.batmap_serve.restype = ctypes.c_int
     L.pair_threshold_noalloc.argtypes = [vp, u32, u32, vp, u64, ctypes.POINTER(u64), vp]
     L.pair_threshold_noalloc.restype = ctypes.c_int
     _lib = L
@@ -295,3 +321,75 @@ def pair_threshold_noalloc(full, n: int, s: int, pairs, stream=None) -> int:
                                   _stream_handle(stream))
     _check(rc, allow=(BATMAP_ERR_CAPACITY,))
     return int(n_out.value)
+
+
+class BatMapPool:
+    """Owning wrapper of a batmap_pool handle."""
+
+    def __init__(self, handle, m, n):
+        self.handle, self.m, self.n = handle, m, n
+
+    def __del__(self):
+        self.free()
+
+    def free(self):
+        if getattr(self, "handle", None):
+            load_library().batmap_pool_free(self.handle)
+            self.handle = None
+
+    @property
+    def info(self) -> dict:
+        nb, by, ne = ctypes.c_uint32(0), ctypes.c_uint64(0), ctypes.c_uint64(0)
+        _check(load_library().batmap_pool_info(self.handle, ctypes.byref(nb), ctypes.byref(by), ctypes.byref(ne)))
+        return {"n_batmaps": nb.value, "batmap_bytes": by.value, "n_elements": ne.value}
+
+
+def batmap_pool_create(m: int, offsets, tids, perm, params: batmap_params | None = None, stream=None) -> BatMapPool:
+    L = load_library()
+    n = int(offsets.numel()) - 1
+    h = ctypes.c_void_p()
+    pp = ctypes.byref(params) if params is not None else None
+    _check(L.batmap_pool_create(pp, int(m), n, _ptr(offsets), _ptr(tids) if tids.numel() else None, _ptr(perm),
+                                _stream_handle(stream), ctypes.byref(h)))
+    return BatMapPool(h, int(m), n)
+
+
+def batmap_pool_free(pool: BatMapPool):
+    pool.free()
+
+
+def batmap_pool_info(pool: BatMapPool) -> dict:
+    return pool.info
+
+
+def _queries_csr(queries):
+    qoff = np.zeros(len(queries) + 1, dtype=np.uint32)
+    qoff[1:] = np.cumsum([len(q) for q in queries])
+    ids = (np.concatenate([np.asarray(q, dtype=np.uint32) for q in queries]) if len(queries)
+           else np.zeros(1, np.uint32))
+    return qoff, np.ascontiguousarray(ids, dtype=np.uint32)
+
+
+def intersect_query(pool: BatMapPool, queries, counts=None, stream=None):
+    """|S_a1 cap ... cap S_ak| for each query (a list of set ids); returns a cuda int64 tensor."""
+    import torch
+    qoff, ids = _queries_csr(queries)
+    if counts is None:
+        counts = torch.zeros(max(len(queries), 1), dtype=torch.int64, device="cuda")
+    _check(load_library().intersect_query(pool.handle, qoff.ctypes.data, ids.ctypes.data, len(queries),
+                                          _ptr(counts), _stream_handle(stream)))
+    return counts[:len(queries)]
+
+
+def batmap_serve(pool: BatMapPool, queries, arrival_s, opts: batmap_serve_opts | None = None, stream=None):
+    """Run the continuous-batching loop; returns (counts uint64, latency_s float64, stats dict)."""
+    qoff, ids = _queries_csr(queries)
+    arr = np.ascontiguousarray(arrival_s, dtype=np.float64)
+    nq = len(queries)
+    counts = np.zeros(max(nq, 1), dtype=np.uint64)
+    lat = np.zeros(max(nq, 1), dtype=np.float64)
+    st = batmap_serve_stats()
+    _check(load_library().batmap_serve(pool.handle, qoff.ctypes.data, ids.ctypes.data, arr.ctypes.data, nq,
+                                       ctypes.byref(opts) if opts is not None else None, counts.ctypes.data,
+                                       lat.ctypes.data, ctypes.byref(st), _stream_handle(stream)))
+    return counts[:nq], lat[:nq], st.as_dict()

@@ -386,7 +386,7 @@ void build_set(batmap_set *S, const uint64_t *d_offsets, const uint32_t *d_tids,
     S->d_fail_off.alloc(n + 1);
     if (T == 0) {
         BM_CUDA(cudaMemsetAsync(S->d_fail_off.p, 0, (n + 1) * sizeof(uint64_t), st));
-        build_schedule(S);
+        if (!S->skip_schedule) build_schedule(S);
         E.record(1, st);
         BM_CUDA(cudaStreamSynchronize(st));
         S->timing.build_ms = E.ms(0, 1);
@@ -498,7 +498,7 @@ void build_set(batmap_set *S, const uint64_t *d_offsets, const uint32_t *d_tids,
     }
 
     E.record(4, st);
-    build_schedule(S);
+    if (!S->skip_schedule) build_schedule(S);
     E.record(1, st);
     BM_CUDA(cudaStreamSynchronize(st));
     S->timing.build_ms = E.ms(0, 1);

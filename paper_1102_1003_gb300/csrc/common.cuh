@@ -147,7 +147,8 @@ struct batmap_set {
     uint32_t m = 0, n = 0, shift = 0, r0 = 0;
     uint64_t n_elements = 0, bytes = 0, n_failed = 0, n_corr = 0;
     double word_pairs = 0.0;
-    uint64_t gen = 0;  // unique build id (batch plans key on it)
+    uint64_t gen = 0;            // unique build id (batch plans key on it)
+    bool skip_schedule = false;  // pool builds need no all-pairs schedule
     cudaStream_t stream = nullptr;
 
     // host metadata

@@ -1,0 +1,529 @@
+// Serving: a device-resident pool of sets answering intersection-size and
+// conjunctive queries (Sec. I: a conjunctive query is a set intersection),
+// with a continuous-batching request loop.
+//
+// Pool storage.  Every set keeps its sorted tidlist.  Sets for which the 8-bit
+// BatMap is compact (|S| >= r_0 / c, Sec. III-A: compression pays only when
+// the set is dense enough) also get a BatMap, built by the same GPU build as
+// pair mining.  A query |S_a1 cap ... cap S_ak| enumerates the smallest set
+// and counts the elements present in every other set (the k-way counting idea
+// of Sec. V): membership in a BatMap is two byte probes -- x is stored in two
+// of the three tables, so tables 1 and 2 always hold at least one copy -- plus
+// a binary search of the set's failed insertions; a set without a BatMap is
+// binary-searched.
+//
+// Work is cut into tasks of up to 1024 elements of the smallest set; one warp
+// runs a task and adds its count with one atomic.
+#include <algorithm>
+#include <chrono>
+#include <memory>
+#include <cstring>
+#include <thread>
+
+#include "common.cuh"
+
+namespace bm {
+
+void build_set(batmap_set *S, const uint64_t *d_offsets, const uint32_t *d_tids, const uint32_t *d_perm);
+
+constexpr uint32_t TASK_ELEMS = 1024;
+constexpr uint32_t MAX_K = 8;
+
+struct QueryDesc {
+    uint32_t k;
+    uint32_t ids[MAX_K];  // smallest set first
+};
+struct ProbeTask {
+    uint32_t q;      // query index within the batch
+    uint32_t begin;  // element range of the smallest set
+    uint32_t end;
+};
+
+struct PoolView {
+    const uint64_t *off;      // [n+1] CSR of all sets
+    const uint32_t *tids;
+    const uint32_t *perm;     // [3*m]
+    const int32_t *bm_index;  // [n] index among BatMap-backed sets or -1
+    const uint64_t *bm_base;  // [nb] byte offset of the BatMap
+    const uint32_t *bm_rlog;  // [nb] log2 r
+    const uint64_t *f_off;    // [nb+1] failed insertions per BatMap-backed set
+    const uint32_t *f_tid;
+    const uint8_t *bm;        // BatMap bytes
+    uint32_t m, shift;
+};
+
+__device__ __forceinline__ bool bsearch_u32(const uint32_t *a, uint64_t lo, uint64_t hi, uint32_t x) {
+    while (lo < hi) {
+        const uint64_t mid = (lo + hi) >> 1;
+        const uint32_t v = a[mid];
+        if (v == x) return true;
+        if (v < x) lo = mid + 1; else hi = mid;
+    }
+    return false;
+}
+
+__device__ __forceinline__ bool member(const PoolView &P, uint32_t c, uint32_t x) {
+    const int32_t b = P.bm_index[c];
+    if (b < 0) return bsearch_u32(P.tids, P.off[c], P.off[c + 1], x);
+    const uint64_t base = P.bm_base[b];
+    const uint32_t r = 1u << P.bm_rlog[b];
+#pragma unroll
+    for (uint32_t t = 0; t < 2; t++) {
+        const uint32_t pi = __ldg(&P.perm[(uint64_t)t * P.m + x]);
+        const uint8_t byte = P.bm[base + slot_of(t, pi, r, P.shift)];
+        if ((uint32_t)(byte & 0x7F) == (pi >> P.shift) + 1u) return true;
+    }
+    return bsearch_u32(P.f_tid, P.f_off[b], P.f_off[b + 1], x);
+}
+
+__global__ void k_probe(PoolView P, const QueryDesc *__restrict__ qs, const ProbeTask *__restrict__ tasks,
+                        uint32_t ntasks, unsigned long long *__restrict__ counts) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < ntasks; w += warps) {
+        const ProbeTask tk = tasks[w];
+        const QueryDesc &Q = qs[tk.q];
+        const uint32_t a = Q.ids[0];
+        const uint64_t a0 = P.off[a];
+        uint32_t cnt = 0;
+        for (uint32_t i = tk.begin + lane; i < tk.end; i += 32) {
+            const uint32_t x = P.tids[a0 + i];
+            bool in_all = true;
+            for (uint32_t t = 1; t < Q.k && in_all; t++) in_all = member(P, Q.ids[t], x);
+            cnt += in_all ? 1u : 0u;
+        }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, d);
+        if (lane == 0 && cnt) atomicAdd(&counts[tk.q], (unsigned long long)cnt);
+    }
+}
+
+// One warp per set: every tid < m and strictly increasing within its set.
+__global__ void k_validate_sets(const uint64_t *__restrict__ off, const uint32_t *__restrict__ tids, uint32_t n,
+                                uint32_t m, int *err) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < n; c += warps) {
+        const uint64_t b = off[c], e = off[c + 1];
+        bool bad = e < b;
+        for (uint64_t i = b + lane; i < e && !bad; i += 32) {
+            const uint32_t x = tids[i];
+            bad = x >= m || (i + 1 < e && !(x < tids[i + 1]));
+        }
+        if (bad) atomicExch(err, 1);
+    }
+}
+
+}  // namespace bm
+
+using namespace bm;
+
+struct batmap_pool {
+    uint32_t m = 0, n = 0;
+    std::vector<uint64_t> h_off;
+    DevBuf<uint64_t> d_off;
+    DevBuf<uint32_t> d_tids, d_perm;
+    DevBuf<int32_t> d_bm_index;
+    DevBuf<uint64_t> d_bm_base, d_fail_off;
+    DevBuf<uint32_t> d_bm_rlog;
+    batmap_set *big = nullptr;
+    uint32_t n_big = 0;
+    uint64_t bm_bytes = 0;
+    PoolView view{};
+    ~batmap_pool() {
+        if (big) {
+            cudaStreamSynchronize(big->stream);
+            delete big;
+        }
+    }
+};
+
+namespace bm {
+
+static void pool_create(const batmap_params *p, uint32_t m, uint32_t n, const uint64_t *d_offsets,
+                        const uint32_t *d_tids, const uint32_t *d_perm, cudaStream_t st, batmap_pool **out) {
+    BM_REQUIRE(out, BATMAP_ERR_ARG, "out is NULL");
+    BM_REQUIRE(m >= 1 && m <= (1u << 30), BATMAP_ERR_ARG, "m must be in [1, 2^30]");
+    BM_REQUIRE(d_perm, BATMAP_ERR_ARG, "d_perm is NULL");
+    batmap_params P;
+    batmap_default_params(&P);
+    if (p) P = *p;
+    auto pool = std::make_unique<batmap_pool>();
+    pool->m = m;
+    pool->n = n;
+    pool->h_off.assign(n + 1, 0);
+    if (n) {
+        BM_REQUIRE(d_offsets, BATMAP_ERR_ARG, "d_offsets is NULL");
+        BM_CUDA(cudaMemcpyAsync(pool->h_off.data(), d_offsets, (n + 1) * 8ull, cudaMemcpyDeviceToHost, st));
+        BM_CUDA(cudaStreamSynchronize(st));
+    }
+    const uint64_t T = pool->h_off[n];
+    pool->d_off.alloc(n + 1);
+    pool->d_tids.alloc(T);
+    pool->d_perm.alloc(3ull * m);
+    if (n) BM_CUDA(cudaMemcpyAsync(pool->d_off.p, d_offsets, (n + 1) * 8ull, cudaMemcpyDeviceToDevice, st));
+    if (T) BM_CUDA(cudaMemcpyAsync(pool->d_tids.p, d_tids, T * 4ull, cudaMemcpyDeviceToDevice, st));
+    BM_CUDA(cudaMemcpyAsync(pool->d_perm.p, d_perm, 3ull * m * 4, cudaMemcpyDeviceToDevice, st));
+    if (n) {
+        DevBuf<int> err(1);
+        BM_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
+        k_validate_sets<<<(unsigned)std::min<uint64_t>((n + 7) / 8, 65535), 256, 0, st>>>(pool->d_off.p,
+                                                                                          pool->d_tids.p, n, m, err.p);
+        BM_CHECK_LAUNCH();
+        int h = 0;
+        BM_CUDA(cudaMemcpyAsync(&h, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        BM_CUDA(cudaStreamSynchronize(st));
+        BM_REQUIRE(h == 0, BATMAP_ERR_ARG, "tids must be strictly increasing per set and < m");
+    }
+
+    // sets whose 8-bit BatMap is compact: c |S| >= r_0
+    uint32_t shift = P.min_shift;
+    while ((uint64_t)m > 127ull << shift) shift++;
+    const uint64_t r0 = 1ull << shift;
+    std::vector<int32_t> bm_index(n, -1);
+    std::vector<uint32_t> big_ids;
+    std::vector<uint64_t> sub_off(1, 0);
+    for (uint32_t i = 0; i < n; i++) {
+        const uint64_t sz = pool->h_off[i + 1] - pool->h_off[i];
+        if (sz && (uint64_t)P.load_num * sz >= r0 * P.load_den) {
+            bm_index[i] = (int32_t)big_ids.size();
+            big_ids.push_back(i);
+            sub_off.push_back(sub_off.back() + sz);
+        }
+    }
+    const uint32_t nb = (uint32_t)big_ids.size();
+    pool->n_big = nb;
+    pool->d_bm_index.alloc(std::max<uint32_t>(n, 1));
+    if (n) BM_CUDA(cudaMemcpyAsync(pool->d_bm_index.p, bm_index.data(), n * 4ull, cudaMemcpyHostToDevice, st));
+    std::vector<uint64_t> base(nb);
+    std::vector<uint32_t> rlog(nb);
+    if (nb) {
+        DevBuf<uint64_t> s_off(nb + 1);
+        DevBuf<uint32_t> s_tids(sub_off.back());
+        BM_CUDA(cudaMemcpyAsync(s_off.p, sub_off.data(), (nb + 1) * 8ull, cudaMemcpyHostToDevice, st));
+        for (uint32_t b = 0; b < nb; b++) {
+            const uint32_t i = big_ids[b];
+            BM_CUDA(cudaMemcpyAsync(s_tids.p + sub_off[b], d_tids + pool->h_off[i],
+                                    (sub_off[b + 1] - sub_off[b]) * 4ull, cudaMemcpyDeviceToDevice, st));
+        }
+        batmap_set *S = new batmap_set();
+        S->params = P;
+        S->params.tile = 0;
+        S->m = m;
+        S->n = nb;
+        S->stream = st;
+        S->skip_schedule = true;
+        try {
+            build_set(S, s_off.p, s_tids.p, d_perm);
+        } catch (...) {
+            delete S;
+            throw;
+        }
+        pool->big = S;
+        pool->bm_bytes = S->bytes;
+        for (uint32_t b = 0; b < nb; b++) {
+            base[b] = S->byte_off[S->rank[b]];
+            uint32_t lg = 0;
+            while ((1u << lg) < S->range[b]) lg++;
+            rlog[b] = lg;
+        }
+    }
+    pool->d_bm_base.alloc(std::max<uint32_t>(nb, 1));
+    pool->d_bm_rlog.alloc(std::max<uint32_t>(nb, 1));
+    if (nb) {
+        BM_CUDA(cudaMemcpyAsync(pool->d_bm_base.p, base.data(), nb * 8ull, cudaMemcpyHostToDevice, st));
+        BM_CUDA(cudaMemcpyAsync(pool->d_bm_rlog.p, rlog.data(), nb * 4ull, cudaMemcpyHostToDevice, st));
+    }
+    pool->view = PoolView{pool->d_off.p,
+                          pool->d_tids.p,
+                          pool->d_perm.p,
+                          pool->d_bm_index.p,
+                          pool->d_bm_base.p,
+                          pool->d_bm_rlog.p,
+                          pool->big ? pool->big->d_fail_off.p : nullptr,
+                          pool->big ? pool->big->d_fail_tid.p : nullptr,
+                          pool->big ? pool->big->d_bm.p : nullptr,
+                          m,
+                          pool->big ? pool->big->shift : shift};
+    BM_CUDA(cudaStreamSynchronize(st));
+    *out = pool.release();
+}
+
+// Host-side preparation of one batch: descriptors with the smallest set first,
+// and the element tasks.  Returns the number of tasks.
+static uint64_t prepare_batch(const batmap_pool *pool, const uint32_t *qoff, const uint32_t *ids, uint64_t q0,
+                              uint64_t q1, std::vector<QueryDesc> *qs, std::vector<ProbeTask> *tasks) {
+    qs->resize(q1 - q0);
+    tasks->clear();
+    for (uint64_t q = q0; q < q1; q++) {
+        const uint32_t k = qoff[q + 1] - qoff[q];
+        BM_REQUIRE(k >= 1 && k <= MAX_K, BATMAP_ERR_ARG, "each query names 1..8 sets");
+        QueryDesc &d = (*qs)[q - q0];
+        d.k = k;
+        for (uint32_t t = 0; t < k; t++) {
+            const uint32_t c = ids[qoff[q] + t];
+            BM_REQUIRE(c < pool->n, BATMAP_ERR_ARG, "query names a set id >= n");
+            d.ids[t] = c;
+        }
+        std::sort(d.ids, d.ids + k, [&](uint32_t a, uint32_t b) {
+            const uint64_t sa = pool->h_off[a + 1] - pool->h_off[a], sb = pool->h_off[b + 1] - pool->h_off[b];
+            return sa < sb || (sa == sb && a < b);
+        });
+        const uint32_t small = (uint32_t)(pool->h_off[d.ids[0] + 1] - pool->h_off[d.ids[0]]);
+        for (uint32_t b = 0; b < small; b += TASK_ELEMS)
+            tasks->push_back({(uint32_t)(q - q0), b, std::min(small, b + TASK_ELEMS)});
+    }
+    return tasks->size();
+}
+
+static uint64_t query_work(const batmap_pool *pool, const uint32_t *qoff, const uint32_t *ids, uint64_t q) {
+    uint64_t small = UINT64_MAX;
+    for (uint32_t t = qoff[q]; t < qoff[q + 1]; t++) {
+        const uint32_t c = ids[t];
+        if (c < pool->n) small = std::min<uint64_t>(small, pool->h_off[c + 1] - pool->h_off[c]);
+    }
+    return (small == UINT64_MAX ? 0 : small) * (qoff[q + 1] - qoff[q]) + 1;
+}
+
+// Staging for one in-flight batch (pinned host + device, fixed capacity).
+struct Slot {
+    cudaStream_t st = nullptr;
+    cudaEvent_t done = nullptr;
+    QueryDesc *h_q = nullptr;
+    ProbeTask *h_t = nullptr;
+    DevBuf<QueryDesc> d_q;
+    DevBuf<ProbeTask> d_t;
+    uint64_t qcap = 0, tcap = 0;
+    uint64_t q0 = 0, q1 = 0, work = 0;
+    bool busy = false;
+    void init(uint64_t qc, uint64_t tc, bool own_stream, cudaStream_t shared) {
+        qcap = qc;
+        tcap = tc;
+        if (own_stream) {
+            BM_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        } else {
+            st = shared;
+        }
+        BM_CUDA(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
+        BM_CUDA(cudaMallocHost(&h_q, qc * sizeof(QueryDesc)));
+        BM_CUDA(cudaMallocHost(&h_t, tc * sizeof(ProbeTask)));
+        d_q.alloc(qc);
+        d_t.alloc(tc);
+    }
+    void destroy(bool own_stream) {
+        if (done) cudaEventDestroy(done);
+        if (own_stream && st) cudaStreamDestroy(st);
+        if (h_q) cudaFreeHost(h_q);
+        if (h_t) cudaFreeHost(h_t);
+        done = nullptr;
+        st = nullptr;
+        h_q = nullptr;
+        h_t = nullptr;
+    }
+};
+
+static void launch_batch(const batmap_pool *pool, Slot &S, const std::vector<QueryDesc> &qs,
+                         const std::vector<ProbeTask> &tasks, unsigned long long *d_counts) {
+    std::memcpy(S.h_q, qs.data(), qs.size() * sizeof(QueryDesc));
+    if (!tasks.empty()) std::memcpy(S.h_t, tasks.data(), tasks.size() * sizeof(ProbeTask));
+    BM_CUDA(cudaMemcpyAsync(S.d_q.p, S.h_q, qs.size() * sizeof(QueryDesc), cudaMemcpyHostToDevice, S.st));
+    if (!tasks.empty())
+        BM_CUDA(cudaMemcpyAsync(S.d_t.p, S.h_t, tasks.size() * sizeof(ProbeTask), cudaMemcpyHostToDevice, S.st));
+    BM_CUDA(cudaMemsetAsync(d_counts + S.q0, 0, (S.q1 - S.q0) * sizeof(unsigned long long), S.st));
+    if (!tasks.empty()) {
+        const uint32_t warps_per_block = 8;
+        const uint64_t blocks = std::min<uint64_t>((tasks.size() + warps_per_block - 1) / warps_per_block, 4096);
+        k_probe<<<(unsigned)blocks, 32 * warps_per_block, 0, S.st>>>(pool->view, S.d_q.p, S.d_t.p,
+                                                                      (uint32_t)tasks.size(), d_counts + S.q0);
+        BM_CHECK_LAUNCH();
+    }
+    BM_CUDA(cudaEventRecord(S.done, S.st));
+}
+
+static void intersect(const batmap_pool *pool, const uint32_t *qoff, const uint32_t *ids, uint32_t nq,
+                      unsigned long long *d_counts, cudaStream_t st) {
+    BM_REQUIRE(pool && qoff && (nq == 0 || ids) && (nq == 0 || d_counts), BATMAP_ERR_ARG, "NULL argument");
+    if (!nq) return;
+    std::vector<QueryDesc> qs;
+    std::vector<ProbeTask> tasks;
+    prepare_batch(pool, qoff, ids, 0, nq, &qs, &tasks);
+    Slot S;
+    S.init(nq, std::max<uint64_t>(tasks.size(), 1), false, st);
+    S.q0 = 0;
+    S.q1 = nq;
+    try {
+        launch_batch(pool, S, qs, tasks, d_counts);
+        BM_CUDA(cudaStreamSynchronize(st));
+    } catch (...) {
+        cudaStreamSynchronize(st);
+        S.destroy(false);
+        throw;
+    }
+    S.destroy(false);
+}
+
+// The continuous-batching request loop.  Queries arrive at h_arrival[q]
+// seconds after the start (non-decreasing).  Whenever a slot is free, the
+// loop gathers the queries that have arrived and not been submitted, up to
+// max_batch queries and while the work in flight stays within the budget
+// (work = elements of the smallest set x sets named), copies their
+// descriptors to the slot's device buffers and launches them on the slot's
+// stream; batches on different slots overlap on the device.  A query's
+// latency is the host time at which its batch's completion event was
+// observed minus its arrival time.
+static void serve(const batmap_pool *pool, const uint32_t *qoff, const uint32_t *ids, const double *arrival,
+                  uint32_t nq, const batmap_serve_opts *o, uint64_t *h_counts, double *h_latency,
+                  batmap_serve_stats *stats, cudaStream_t st) {
+    BM_REQUIRE(pool && qoff && arrival && h_counts && h_latency, BATMAP_ERR_ARG, "NULL argument");
+    batmap_serve_opts opt{64, 4, 1ull << 26, 0};
+    if (o) opt = *o;
+    BM_REQUIRE(opt.max_batch >= 1 && opt.slots >= 1 && opt.slots <= 64, BATMAP_ERR_ARG, "bad serve options");
+    for (uint32_t q = 1; q < nq; q++)
+        BM_REQUIRE(arrival[q] >= arrival[q - 1], BATMAP_ERR_ARG, "arrival times must be non-decreasing");
+    std::vector<uint64_t> work(nq);
+    uint64_t max_tasks = 1, max_work = 1;
+    for (uint32_t q = 0; q < nq; q++) {
+        work[q] = query_work(pool, qoff, ids, q);
+        max_work = std::max(max_work, work[q]);
+    }
+    // task capacity of a slot: the largest batch the budget admits
+    for (uint32_t q = 0; q < nq; q++) {
+        uint64_t small = work[q] / std::max<uint32_t>(1, qoff[q + 1] - qoff[q]);
+        max_tasks = std::max<uint64_t>(max_tasks, small / TASK_ELEMS + 1);
+    }
+    const uint64_t budget = std::max<uint64_t>(opt.work_budget, max_work);
+    const uint64_t tcap = std::max<uint64_t>(max_tasks * 2, budget / TASK_ELEMS + (uint64_t)opt.max_batch);
+    DevBuf<unsigned long long> d_counts(std::max<uint32_t>(nq, 1));
+    std::vector<Slot> slots(opt.slots);
+    for (auto &s : slots) s.init(opt.max_batch, tcap, true, st);
+    std::vector<QueryDesc> qs;
+    std::vector<ProbeTask> tasks;
+    using clk = std::chrono::steady_clock;
+    const auto t0 = clk::now();
+    auto now_s = [&] { return std::chrono::duration<double>(clk::now() - t0).count(); };
+    uint64_t next = 0, done = 0, inflight_work = 0, batches = 0, max_inflight = 0, inflight = 0;
+    try {
+        while (done < nq) {
+            const double t = now_s();
+            bool progressed = false;
+            for (auto &s : slots) {
+                if (!s.busy) continue;
+                cudaError_t e = cudaEventQuery(s.done);
+                if (e == cudaErrorNotReady) continue;
+                BM_CUDA(e);
+                const double tc = now_s();
+                for (uint64_t q = s.q0; q < s.q1; q++) h_latency[q] = tc - arrival[q];
+                done += s.q1 - s.q0;
+                inflight_work -= s.work;
+                inflight--;
+                s.busy = false;
+                progressed = true;
+            }
+            for (auto &s : slots) {
+                if (s.busy || next >= nq || arrival[next] > t) continue;
+                uint64_t q1 = next, w = 0;
+                while (q1 < nq && arrival[q1] <= t && q1 - next < opt.max_batch &&
+                       (q1 == next ? inflight_work + work[q1] <= budget || inflight == 0
+                                   : inflight_work + w + work[q1] <= budget))
+                    w += work[q1++];
+                if (q1 == next) break;  // budget full: wait for completions
+                prepare_batch(pool, qoff, ids, next, q1, &qs, &tasks);
+                if (tasks.size() > s.tcap) {  // admit fewer queries
+                    q1 = next + 1;
+                    prepare_batch(pool, qoff, ids, next, q1, &qs, &tasks);
+                    BM_REQUIRE(tasks.size() <= s.tcap, BATMAP_ERR_INTERNAL, "task capacity");
+                    w = work[next];
+                }
+                s.q0 = next;
+                s.q1 = q1;
+                s.work = w;
+                launch_batch(pool, s, qs, tasks, d_counts.p);
+                s.busy = true;
+                inflight++;
+                inflight_work += w;
+                max_inflight = std::max(max_inflight, inflight);
+                batches++;
+                next = q1;
+                progressed = true;
+            }
+            if (!progressed) {
+                const double wait = next < nq ? arrival[next] - now_s() : 0.0;
+                if (wait > 200e-6) std::this_thread::sleep_for(std::chrono::microseconds(50));
+            }
+        }
+        const double makespan = now_s();
+        if (nq) BM_CUDA(cudaMemcpy(h_counts, d_counts.p, nq * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+        if (stats) {
+            std::memset(stats, 0, sizeof(*stats));
+            stats->makespan_s = makespan;
+            stats->batches = batches;
+            stats->max_inflight = max_inflight;
+            std::vector<double> lat(h_latency, h_latency + nq);
+            std::sort(lat.begin(), lat.end());
+            if (nq) {
+                stats->p50_s = lat[(size_t)(0.50 * (nq - 1))];
+                stats->p99_s = lat[(size_t)(0.99 * (nq - 1))];
+                stats->max_s = lat.back();
+                stats->queries_per_s = nq / std::max(makespan, 1e-9);
+            }
+        }
+    } catch (...) {
+        for (auto &s : slots) {
+            if (s.st) cudaStreamSynchronize(s.st);
+            s.destroy(true);
+        }
+        throw;
+    }
+    for (auto &s : slots) {
+        cudaStreamSynchronize(s.st);
+        s.destroy(true);
+    }
+}
+
+}  // namespace bm
+
+extern "C" {
+
+#define BM_GUARD(body)                              \
+    try {                                           \
+        body;                                       \
+        return BATMAP_OK;                           \
+    } catch (const bm::Error &e) {                  \
+        bm::set_error(e.msg);                       \
+        return e.code;                              \
+    } catch (...) {                                 \
+        bm::set_error("unexpected internal error"); \
+        return BATMAP_ERR_INTERNAL;                 \
+    }
+
+batmap_status batmap_pool_create(const batmap_params *p, uint32_t m, uint32_t n, const uint64_t *d_offsets,
+                                 const uint32_t *d_tids, const uint32_t *d_perm, cudaStream_t stream,
+                                 batmap_pool **out) {
+    BM_GUARD(bm::pool_create(p, m, n, d_offsets, d_tids, d_perm, stream, out));
+}
+
+void batmap_pool_free(batmap_pool *pool) { delete pool; }
+
+batmap_status batmap_pool_info(const batmap_pool *pool, uint32_t *n_batmaps, uint64_t *batmap_bytes,
+                               uint64_t *n_elements) {
+    BM_GUARD({
+        BM_REQUIRE(pool, BATMAP_ERR_ARG, "NULL pool");
+        if (n_batmaps) *n_batmaps = pool->n_big;
+        if (batmap_bytes) *batmap_bytes = pool->bm_bytes;
+        if (n_elements) *n_elements = pool->h_off[pool->n];
+    });
+}
+
+batmap_status intersect_query(const batmap_pool *pool, const uint32_t *h_qoff, const uint32_t *h_ids,
+                              uint32_t n_queries, uint64_t *d_counts, cudaStream_t stream) {
+    BM_GUARD(bm::intersect(pool, h_qoff, h_ids, n_queries, reinterpret_cast<unsigned long long *>(d_counts),
+                           stream));
+}
+
+batmap_status batmap_serve(const batmap_pool *pool, const uint32_t *h_qoff, const uint32_t *h_ids,
+                           const double *h_arrival_s, uint32_t n_queries, const batmap_serve_opts *opts,
+                           uint64_t *h_counts, double *h_latency_s, batmap_serve_stats *stats, cudaStream_t stream) {
+    BM_GUARD(bm::serve(pool, h_qoff, h_ids, h_arrival_s, n_queries, opts, h_counts, h_latency_s, stats, stream));
+}
+
+}  // extern "C"
