@@ -341,19 +341,105 @@ def run_mine(args, inst, rank, world):
         dist.destroy_process_group()
 
 
+def run_serve(args):
+    """Serving workload: pool of sets over 2^26 with Zipf sizes on [10, 1e6],
+    Poisson-arriving queries (80% pairs, 20% 3..8-way), continuous batching."""
+    import math
+    import torch
+    import paper_1102_1003_gb300 as pkg
+    import oracle
+    U, lo, hi, seed = 1 << 26, 10, 10**6, 5
+    count = args.pool_sets
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    sizes = datagen.pool_sizes(count, lo, hi, seed)
+    ub = int(sum(int(k + 6 * math.sqrt(k) + 16) for k in sizes))
+    t0 = time.perf_counter()
+    d_tids = torch.empty(ub, dtype=torch.int32, device=dev)
+    real = np.zeros(count, dtype=np.int64)
+    pos = 0
+    for a, got, arr in datagen.pool_blocks(count, U, lo, hi, seed, workers=os.cpu_count() or 8):
+        d_tids[pos:pos + arr.size].copy_(torch.from_numpy(arr.view(np.int32)))
+        real[a:a + got.size] = got
+        pos += arr.size
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    offsets = np.zeros(count + 1, dtype=np.uint64)
+    offsets[1:] = np.cumsum(real)
+    d_off = torch.from_numpy(offsets.view(np.int64)).to(dev)
+    perm = torch.from_numpy(datagen.permutations(U, seed).view(np.int32)).to(dev)
+    t0 = time.perf_counter()
+    pool = pkg.batmap_pool_create(U, d_off, d_tids[:pos], perm)
+    build_s = time.perf_counter() - t0
+    info = pool.info
+    del d_tids
+    torch.cuda.empty_cache()
+    rng = np.random.default_rng(77)
+    nq = args.queries
+    queries = []
+    for _ in range(nq):
+        k = 2 if rng.random() < 0.8 else int(rng.integers(3, 9))
+        queries.append(rng.integers(0, count, k).tolist())
+    opts = pkg.batmap_serve_opts(max_batch=args.max_batch, slots=args.slots, work_budget=1 << 26, reserved=0)
+    pkg.batmap_serve(pool, queries[:2000], np.zeros(2000), opts)  # warm-up
+    counts, lat, st_max = pkg.batmap_serve(pool, queries, np.zeros(nq), opts)
+    qps_max = st_max["queries_per_s"]
+    # one query per launch, no batching, for comparison
+    n_plain = min(nq, 3000)
+    t0 = time.perf_counter()
+    for q in range(n_plain):
+        pkg.intersect_query(pool, [queries[q]])
+    torch.cuda.synchronize()
+    qps_plain = n_plain / (time.perf_counter() - t0)
+    loads = []
+    for f in (0.25, 0.5, 0.75, 0.9):
+        arrival = np.cumsum(np.random.default_rng(int(f * 100)).exponential(1.0 / (f * qps_max), nq))
+        c2, lat2, st2 = pkg.batmap_serve(pool, queries, arrival, opts)
+        assert np.array_equal(c2, counts)
+        loads.append({"offered_fraction": f, "offered_qps": f * qps_max, "achieved_qps": st2["queries_per_s"],
+                      "p50_ms": 1e3 * st2["p50_s"], "p99_ms": 1e3 * st2["p99_s"], "batches": st2["batches"],
+                      "max_inflight": st2["max_inflight"]})
+    # parity on a sample: regenerate the named sets on the CPU and run the oracle
+    sample = np.random.default_rng(5).choice(nq, min(nq, 300), replace=False)
+    ids = sorted({c for q in sample for c in queries[q]})
+    remap = {c: j for j, c in enumerate(ids)}
+    sub = datagen.from_lists([datagen.pool_set(U, int(sizes[c]), seed, c) for c in ids], U)
+    ref = oracle.kway_counts(sub.offsets, sub.tids, [[remap[c] for c in queries[q]] for q in sample])
+    exact = bool(np.array_equal(counts[sample], ref))
+    line = {"metric": "serving queries/sec and p50/p99 latency", "workload": "serve", "unit": "queries/s",
+            "value": qps_max, "plain_one_query_per_launch_qps": qps_plain, "loads": loads,
+            "closed_loop": {"p50_ms": 1e3 * st_max["p50_s"], "p99_ms": 1e3 * st_max["p99_s"],
+                            "batches": st_max["batches"], "max_inflight": st_max["max_inflight"]},
+            "config": {"pool_sets": count, "universe": U, "sizes": "Zipf(1) on [10, 1e6]",
+                       "elements": int(info["n_elements"]), "batmap_sets": info["n_batmaps"],
+                       "batmap_bytes": int(info["batmap_bytes"]), "queries": nq,
+                       "mix": "80% pairwise, 20% k in 3..8, uniform set ids", "max_batch": args.max_batch,
+                       "slots": args.slots},
+            "gen_s": gen_s, "pool_build_s": build_s, "parity_sample": {"queries": int(sample.size), "exact": exact}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["mine", "reference"], default="mine")
-    ap.add_argument("--workload", choices=sorted(WORKLOAD_DESC), default="cfg2")
+    ap.add_argument("--workload", choices=sorted(WORKLOAD_DESC) + ["serve"], default="cfg2")
+    ap.add_argument("--pool-sets", type=int, default=100_000, help="serving pool size (serve workload)")
+    ap.add_argument("--queries", type=int, default=200_000, help="queries per serving run (serve workload)")
+    ap.add_argument("--max-batch", type=int, default=256)
+    ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-dense", action="store_true", help="skip the dense tensor-core comparison leg")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.workload == "serve":
+        if rank == 0:
+            run_serve(args)
+        return
     inst = datagen.config_instance(args.workload)
     if args.impl == "reference":
         run_reference(args, inst, rank, world)

@@ -183,9 +183,53 @@ def pool_sizes(count: int, lo: int, hi: int, seed: int) -> np.ndarray:
     return np.minimum(hi, np.floor(lo * np.exp(u * math.log((hi + 1) / lo)))).astype(np.int64)
 
 
+def pool_set(universe: int, size: int, seed: int, i: int) -> np.ndarray:
+    """Members of pool set i (Bernoulli with p = size / universe)."""
+    return bernoulli_item(_item_rng(seed, i), universe, float(size) / universe)
+
+
+def _pool_block(args):
+    """Worker: generate sets [a, b) into a new shared-memory block; returns
+    (name, sizes) and leaves the block for the parent to attach and unlink."""
+    from multiprocessing import shared_memory
+    universe, sizes, seed, a = args
+    parts = [pool_set(universe, int(k), seed, a + j) for j, k in enumerate(sizes)]
+    total = sum(p.size for p in parts)
+    shm = shared_memory.SharedMemory(create=True, size=max(4 * total, 4))
+    out = np.ndarray((total,), dtype=np.uint32, buffer=shm.buf)
+    pos = 0
+    for p in parts:
+        out[pos:pos + p.size] = p
+        pos += p.size
+    name = shm.name
+    shm.close()
+    return name, np.array([p.size for p in parts], dtype=np.int64)
+
+
+def pool_blocks(count: int, universe: int, lo: int, hi: int, seed: int, workers: int = 8, block: int = 2000):
+    """The serving pool generated in parallel worker processes (spawned, so it
+    is safe to call after CUDA is initialised).  Yields (first_set, sizes,
+    tids) per block of sets, tids a uint32 array in shared memory that is
+    released when the generator advances.  Same sets as pool_tidlists."""
+    import multiprocessing as mp
+    from multiprocessing import shared_memory
+    sizes = pool_sizes(count, lo, hi, seed)
+    jobs = [(universe, sizes[a:a + block], seed, a) for a in range(0, count, block)]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(workers) as pool:
+        for (a, (name, got)) in zip(range(0, count, block), pool.imap(_pool_block, jobs)):
+            shm = shared_memory.SharedMemory(name=name)
+            try:
+                arr = np.ndarray((int(got.sum()),), dtype=np.uint32, buffer=shm.buf)
+                yield a, got, arr
+                del arr
+            finally:
+                shm.close()
+                shm.unlink()
+
+
 def pool_tidlists(count: int, universe: int, lo: int, hi: int, seed: int) -> Instance:
     """Serving pool: `count` sets over [0, universe) with Zipf sizes, uniform members."""
     sizes = pool_sizes(count, lo, hi, seed)
-    lists = [bernoulli_item(_item_rng(seed, i), universe, float(sizes[i]) / universe)
-             for i in range(count)]
+    lists = [pool_set(universe, int(sizes[i]), seed, i) for i in range(count)]
     return from_lists(lists, universe, 0, "pool")

@@ -125,17 +125,11 @@ struct batmap_pool {
     DevBuf<uint32_t> d_tids, d_perm;
     DevBuf<int32_t> d_bm_index;
     DevBuf<uint64_t> d_bm_base, d_fail_off;
-    DevBuf<uint32_t> d_bm_rlog;
-    batmap_set *big = nullptr;
-    uint32_t n_big = 0;
-    uint64_t bm_bytes = 0;
+    DevBuf<uint32_t> d_bm_rlog, d_fail_tid;
+    DevBuf<uint8_t> d_bm;
+    uint32_t n_big = 0, shift = 0;
+    uint64_t bm_bytes = 0, n_failed = 0;
     PoolView view{};
-    ~batmap_pool() {
-        if (big) {
-            cudaStreamSynchronize(big->stream);
-            delete big;
-        }
-    }
 };
 
 namespace bm {
@@ -197,54 +191,88 @@ static void pool_create(const batmap_params *p, uint32_t m, uint32_t n, const ui
     if (n) BM_CUDA(cudaMemcpyAsync(pool->d_bm_index.p, bm_index.data(), n * 4ull, cudaMemcpyHostToDevice, st));
     std::vector<uint64_t> base(nb);
     std::vector<uint32_t> rlog(nb);
+    std::vector<uint64_t> f_off(nb + 1, 0);
     if (nb) {
-        DevBuf<uint64_t> s_off(nb + 1);
-        DevBuf<uint32_t> s_tids(sub_off.back());
-        BM_CUDA(cudaMemcpyAsync(s_off.p, sub_off.data(), (nb + 1) * 8ull, cudaMemcpyHostToDevice, st));
+        // BatMap bytes of every big set (same sizing rule as the build)
+        uint64_t total_bytes = 0;
+        std::vector<uint64_t> bytes_of(nb);
         for (uint32_t b = 0; b < nb; b++) {
-            const uint32_t i = big_ids[b];
-            BM_CUDA(cudaMemcpyAsync(s_tids.p + sub_off[b], d_tids + pool->h_off[i],
-                                    (sub_off[b + 1] - sub_off[b]) * 4ull, cudaMemcpyDeviceToDevice, st));
+            const uint64_t sz = sub_off[b + 1] - sub_off[b];
+            const uint64_t need = (P.load_num * sz + P.load_den - 1) / P.load_den;
+            uint64_t r = 1;
+            while (r < need) r <<= 1;
+            bytes_of[b] = 3 * std::max<uint64_t>(r, r0);
+            total_bytes += bytes_of[b];
         }
-        batmap_set *S = new batmap_set();
-        S->params = P;
-        S->params.tile = 0;
-        S->m = m;
-        S->n = nb;
-        S->stream = st;
-        S->skip_schedule = true;
-        try {
-            build_set(S, s_off.p, s_tids.p, d_perm);
-        } catch (...) {
-            delete S;
-            throw;
+        pool->d_bm.alloc(total_bytes);
+        std::vector<uint32_t> f_chunks_tid;
+        uint64_t bm_pos = 0, f_pos = 0;
+        // build in chunks of at most ~4 GB of BatMaps so the placement scratch
+        // (4 bytes per slot) stays bounded
+        for (uint32_t c0 = 0; c0 < nb;) {
+            uint32_t c1 = c0;
+            uint64_t cb = 0;
+            while (c1 < nb && (c1 == c0 || cb + bytes_of[c1] <= (4ull << 30))) cb += bytes_of[c1++];
+            const uint32_t cn = c1 - c0;
+            std::vector<uint64_t> coff(cn + 1, 0);
+            for (uint32_t j = 0; j < cn; j++) coff[j + 1] = coff[j] + (sub_off[c0 + j + 1] - sub_off[c0 + j]);
+            DevBuf<uint64_t> s_off(cn + 1);
+            DevBuf<uint32_t> s_tids(coff[cn]);
+            BM_CUDA(cudaMemcpyAsync(s_off.p, coff.data(), (cn + 1) * 8ull, cudaMemcpyHostToDevice, st));
+            for (uint32_t j = 0; j < cn; j++) {
+                const uint32_t i = big_ids[c0 + j];
+                BM_CUDA(cudaMemcpyAsync(s_tids.p + coff[j], d_tids + pool->h_off[i], (coff[j + 1] - coff[j]) * 4ull,
+                                        cudaMemcpyDeviceToDevice, st));
+            }
+            batmap_set S;
+            S.params = P;
+            S.params.tile = 0;
+            S.m = m;
+            S.n = cn;
+            S.stream = st;
+            S.skip_schedule = true;
+            build_set(&S, s_off.p, s_tids.p, d_perm);
+            pool->shift = S.shift;
+            BM_CUDA(cudaMemcpyAsync(pool->d_bm.p + bm_pos, S.d_bm.p, S.bytes, cudaMemcpyDeviceToDevice, st));
+            std::vector<uint64_t> cf(cn + 1, 0);
+            BM_CUDA(cudaMemcpyAsync(cf.data(), S.d_fail_off.p, (cn + 1) * 8ull, cudaMemcpyDeviceToHost, st));
+            BM_CUDA(cudaStreamSynchronize(st));
+            if (S.n_failed) {
+                std::vector<uint32_t> ft(S.n_failed);
+                BM_CUDA(cudaMemcpy(ft.data(), S.d_fail_tid.p, S.n_failed * 4ull, cudaMemcpyDeviceToHost));
+                f_chunks_tid.insert(f_chunks_tid.end(), ft.begin(), ft.end());
+            }
+            for (uint32_t j = 0; j < cn; j++) {
+                base[c0 + j] = bm_pos + S.byte_off[S.rank[j]];
+                uint32_t lg = 0;
+                while ((1u << lg) < S.range[j]) lg++;
+                rlog[c0 + j] = lg;
+                f_off[c0 + j + 1] = f_pos + cf[j + 1];
+            }
+            f_pos += S.n_failed;
+            bm_pos += S.bytes;
+            pool->n_failed += S.n_failed;
+            c0 = c1;
         }
-        pool->big = S;
-        pool->bm_bytes = S->bytes;
-        for (uint32_t b = 0; b < nb; b++) {
-            base[b] = S->byte_off[S->rank[b]];
-            uint32_t lg = 0;
-            while ((1u << lg) < S->range[b]) lg++;
-            rlog[b] = lg;
-        }
+        pool->bm_bytes = bm_pos;
+        pool->d_fail_tid.alloc(std::max<uint64_t>(f_chunks_tid.size(), 1));
+        if (!f_chunks_tid.empty())
+            BM_CUDA(cudaMemcpyAsync(pool->d_fail_tid.p, f_chunks_tid.data(), f_chunks_tid.size() * 4ull,
+                                    cudaMemcpyHostToDevice, st));
+        BM_CUDA(cudaStreamSynchronize(st));
     }
+    pool->d_fail_off.alloc(nb + 1);
+    BM_CUDA(cudaMemcpyAsync(pool->d_fail_off.p, f_off.data(), (nb + 1) * 8ull, cudaMemcpyHostToDevice, st));
     pool->d_bm_base.alloc(std::max<uint32_t>(nb, 1));
     pool->d_bm_rlog.alloc(std::max<uint32_t>(nb, 1));
     if (nb) {
         BM_CUDA(cudaMemcpyAsync(pool->d_bm_base.p, base.data(), nb * 8ull, cudaMemcpyHostToDevice, st));
         BM_CUDA(cudaMemcpyAsync(pool->d_bm_rlog.p, rlog.data(), nb * 4ull, cudaMemcpyHostToDevice, st));
     }
-    pool->view = PoolView{pool->d_off.p,
-                          pool->d_tids.p,
-                          pool->d_perm.p,
-                          pool->d_bm_index.p,
-                          pool->d_bm_base.p,
-                          pool->d_bm_rlog.p,
-                          pool->big ? pool->big->d_fail_off.p : nullptr,
-                          pool->big ? pool->big->d_fail_tid.p : nullptr,
-                          pool->big ? pool->big->d_bm.p : nullptr,
-                          m,
-                          pool->big ? pool->big->shift : shift};
+    pool->view = PoolView{pool->d_off.p,     pool->d_tids.p,     pool->d_perm.p,
+                          pool->d_bm_index.p, pool->d_bm_base.p, pool->d_bm_rlog.p,
+                          pool->d_fail_off.p, pool->d_fail_tid.p, pool->d_bm.p,
+                          m,                  nb ? pool->shift : shift};
     BM_CUDA(cudaStreamSynchronize(st));
     *out = pool.release();
 }
