@@ -341,6 +341,86 @@ def run_mine(args, inst, rank, world):
         dist.destroy_process_group()
 
 
+def run_batch(args):
+    """Batched workload: 64 instances (m log-uniform in [1e4, 1e6], n uniform in
+    [100, 4000], density uniform in [1%, 10%], Zipf items); one batched,
+    graph-captured persistent launch vs 64 plain pair_support_all calls."""
+    import torch
+    import paper_1102_1003_gb300 as pkg
+    import oracle
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    specs = datagen.batch_specs(args.instances, 1000)
+    t0 = time.perf_counter()
+    insts = datagen.batch_instances(specs, workers=os.cpu_count() or 8)
+    gen_s = time.perf_counter() - t0
+    sets, bufs, npairs = [], [], 0
+    t0 = time.perf_counter()
+    for q, inst in enumerate(insts):
+        off = torch.from_numpy(inst.offsets.view(np.int64)).to(dev)
+        tids = torch.from_numpy(inst.tids.view(np.int32)).to(dev)
+        perm = torch.from_numpy(datagen.permutations(inst.m, inst.s + q).view(np.int32)).to(dev)
+        sets.append(pkg.batmap_build(inst.m, off, tids, perm))
+        npairs += inst.n * (inst.n - 1) // 2
+        del off, tids, perm
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    # output sizes from one plain pass
+    n_out = [pkg.pair_support_all(b, i.s)[0] for b, i in zip(sets, insts)]
+    bufs = [torch.empty((max(k, 1), 3), dtype=torch.int32, device=dev) for k in n_out]
+    s_list = [i.s for i in insts]
+    eff = None
+    if not args.no_autotune:
+        eff = pkg.batmap_autotune(sets)
+
+    def plain():
+        return [pkg.pair_support_all(b, s, pairs=buf)[0] for b, s, buf in zip(sets, s_list, bufs)]
+
+    def batched():
+        return pkg.pair_support_batch(sets, s_list, bufs)
+
+    results = {}
+    for name, fn in (("plain", plain), ("batched", batched)):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        stream = torch.cuda.current_stream()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            got = fn()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        el = ev0.elapsed_time(ev1) / 1e3
+        results[name] = {"value": npairs * args.steps / el, "ms_per_step": 1e3 * el / args.steps}
+        assert list(got) == n_out, name
+    # batched and plain give identical outputs; a sampled oracle check per instance
+    batch_pairs = [b[:k].cpu().numpy().copy() for b, k in zip(bufs, n_out)]
+    plain()
+    same = all(np.array_equal(b[:k].cpu().numpy(), bp) for b, k, bp in zip(bufs, n_out, batch_pairs))
+    rng = np.random.default_rng(3)
+    exact = True
+    for q in rng.choice(len(insts), 6, replace=False):
+        inst = insts[q]
+        full = torch.empty(inst.n * (inst.n - 1) // 2, dtype=torch.int32, device=dev)
+        pkg.pair_support_all(sets[q], inst.s, full=full)
+        ii = rng.integers(0, inst.n - 1, 400)
+        jj = np.minimum(inst.n - 1, ii + 1 + rng.integers(0, inst.n, 400) % np.maximum(inst.n - 1 - ii, 1))
+        ref = oracle.pairs_list(inst.offsets, inst.tids, ii, jj, threads=os.cpu_count() or 4)
+        idx = ii * inst.n - ii * (ii + 1) // 2 + (jj - ii - 1)
+        exact &= bool(np.array_equal(full.cpu().numpy()[idx].astype(np.uint32), ref))
+    line = {"metric": METRIC, "workload": "batch", "unit": UNIT, "value": results["batched"]["value"],
+            "ms_per_step": results["batched"]["ms_per_step"], "plain": results["plain"],
+            "speedup_batched_over_plain": results["batched"]["value"] / results["plain"]["value"],
+            "config": {"instances": len(insts), "pairs": npairs, "tids": int(sum(i.tids.size for i in insts)),
+                       "m_range": [min(i.m for i in insts), max(i.m for i in insts)],
+                       "n_range": [min(i.n for i in insts), max(i.n for i in insts)],
+                       "autotuned": eff is not None},
+            "shape_eff": eff, "gen_s": gen_s, "build_s": build_s,
+            "batched_equals_plain": same, "oracle_sample_exact": exact}
+    print(json.dumps(line), flush=True)
+
+
 def run_serve(args):
     """Serving workload: pool of sets over 2^26 with Zipf sizes on [10, 1e6],
     Poisson-arriving queries (80% pairs, 20% 3..8-way), continuous batching."""
@@ -425,7 +505,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["mine", "reference"], default="mine")
-    ap.add_argument("--workload", choices=sorted(WORKLOAD_DESC) + ["serve"], default="cfg2")
+    ap.add_argument("--workload", choices=sorted(WORKLOAD_DESC) + ["serve", "batch"], default="cfg2")
+    ap.add_argument("--instances", type=int, default=64, help="instances (batch workload)")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--pool-sets", type=int, default=100_000, help="serving pool size (serve workload)")
     ap.add_argument("--queries", type=int, default=200_000, help="queries per serving run (serve workload)")
     ap.add_argument("--max-batch", type=int, default=256)
@@ -436,9 +518,9 @@ def main():
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
-    if args.workload == "serve":
+    if args.workload in ("serve", "batch"):
         if rank == 0:
-            run_serve(args)
+            (run_serve if args.workload == "serve" else run_batch)(args)
         return
     inst = datagen.config_instance(args.workload)
     if args.impl == "reference":

@@ -175,6 +175,19 @@ def batch_specs(k: int = 64, seed0: int = 1000, m_range=(1e4, 1e6), n_range=(100
     return specs
 
 
+def batch_instance(spec: dict) -> Instance:
+    """One instance of the batched workload from its spec (see batch_specs)."""
+    return zipf_tidlists(spec["m"], spec["n"], spec["density"], spec["seed"], 1.0, spec["s"],
+                         f"batch{spec['seed']}")
+
+
+def batch_instances(specs, workers: int = 8):
+    """All instances of the batched workload, generated in spawned worker processes."""
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(workers) as pool:
+        return pool.map(batch_instance, specs)
+
+
 def pool_sizes(count: int, lo: int, hi: int, seed: int) -> np.ndarray:
     """Discrete Zipf(1) set sizes on [lo, hi]: P(k) proportional to 1/k."""
     g = np.random.default_rng([int(seed), 0x9001])

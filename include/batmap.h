@@ -181,6 +181,19 @@ batmap_status pair_support_host(const batmap_params *p, uint32_t m, uint32_t n,
                                 uint64_t cap, uint64_t *n_out, cudaStream_t stream);
 
 /*
+ * Autotuner of the compare schedule.  Runs the all-pairs compare of (up to
+ * four of the largest of) the given sets once per tile shape, each shape
+ * alone, and measures its throughput in padded word pairs per second.  The
+ * relative throughputs become the scheduler's shape costs for every later
+ * batmap_build in the process, and all k sets are rescheduled with them (the
+ * width class -> tile shape choice and the split of column words into work
+ * units).
+ *   shape_eff : optional host double[12], receives the relative throughputs.
+ * Synchronises the stream.
+ */
+batmap_status batmap_autotune(batmap_set *const *sets, uint32_t k, double *shape_eff, cudaStream_t stream);
+
+/*
  * Device-side durations of the most recent batmap_build / pair_support_all
  * on a set, measured with CUDA events recorded on the call's stream around
  * each phase (milliseconds; 0 for a phase that did not run).

@@ -28,7 +28,7 @@ EXPORTED = [
     "batmap_get_info", "batmap_export_layout", "pair_support_all", "pair_support_host",
     "pair_support_batch", "batmap_get_timing", "batmap_kernel_launches", "pair_threshold_noalloc",
     "pair_support_dense", "batmap_pool_create", "batmap_pool_free", "batmap_pool_info", "intersect_query",
-    "batmap_serve",
+    "batmap_serve", "batmap_autotune",
 ]
 
 
@@ -137,6 +137,8 @@ def load_library(path: str = LIB_PATH):
     L.batmap_serve.argtypes = [vp, vp, vp, vp, u32, ctypes.POINTER(batmap_serve_opts), vp, vp,
                                ctypes.POINTER(batmap_serve_stats), vp]
     L.batmap_serve.restype = ctypes.c_int
+    L.batmap_autotune.argtypes = [ctypes.POINTER(vp), u32, ctypes.POINTER(ctypes.c_double), vp]
+    L.batmap_autotune.restype = ctypes.c_int
     L.pair_threshold_noalloc.argtypes = [vp, u32, u32, vp, u64, ctypes.POINTER(u64), vp]
     L.pair_threshold_noalloc.restype = ctypes.c_int
     _lib = L
@@ -277,6 +279,17 @@ def pair_support_dense(m: int, offsets, tids, s: int, pairs=None, full=None, str
     _check(rc, allow=(BATMAP_ERR_CAPACITY,))
     k = min(int(n_out.value), cap)
     return int(n_out.value), pairs.view(-1, 3)[:k], t.as_dict()
+
+
+def batmap_autotune(sets, stream=None):
+    """Measure every tile shape on these sets, adopt the result for scheduling and
+    reschedule them; returns the relative throughput per shape (1..12)."""
+    L = load_library()
+    k = len(sets)
+    handles = (ctypes.c_void_p * k)(*[b.handle for b in sets])
+    eff = (ctypes.c_double * 12)()
+    _check(L.batmap_autotune(handles, k, eff, _stream_handle(stream)))
+    return list(eff)
 
 
 def pair_support_batch(sets, s_list, pairs_list, full_list=None, stream=None):

@@ -158,6 +158,89 @@ void run_batch(batmap_set *const *sets, const uint32_t *s, uint32_t k, batmap_ou
     if (overflow) throw Error{BATMAP_ERR_CAPACITY, "an instance's d_pairs is too small (see n_out)"};
 }
 
+// ---- autotuner ----------------------------------------------------------------
+//
+// Measures the throughput (padded word pairs per second) of every tile shape
+// on the caller's own sets: for each shape, the sampled sets are scheduled
+// with that shape alone and compared once, timed with events.  The relative
+// throughputs replace the built-in efficiency prior of the scheduler, and
+// every given set is rescheduled with them.
+
+static std::mutex g_tune_mu;
+static bool g_tuned = false;
+static double g_tuned_eff[NUM_SHAPES];
+
+bool tuned_shape_eff(double *eff) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    if (!g_tuned) return false;
+    for (int s = 0; s < NUM_SHAPES; s++) eff[s] = g_tuned_eff[s];
+    return true;
+}
+
+void autotune(batmap_set *const *sets, uint32_t k, double *eff_out, cudaStream_t st) {
+    BM_REQUIRE(sets && k, BATMAP_ERR_ARG, "no sets to tune on");
+    std::vector<uint32_t> idx;
+    for (uint32_t q = 0; q < k; q++) {
+        BM_REQUIRE(sets[q], BATMAP_ERR_ARG, "NULL set");
+        if (sets[q]->n > 1) idx.push_back(q);
+    }
+    BM_REQUIRE(!idx.empty(), BATMAP_ERR_ARG, "no set with a pair to tune on");
+    std::sort(idx.begin(), idx.end(), [&](uint32_t a, uint32_t b) { return sets[a]->word_pairs > sets[b]->word_pairs; });
+    if (idx.size() > 4) idx.resize(4);
+    std::vector<InstView> views;
+    for (uint32_t q : idx) {
+        batmap_set *S = sets[q];
+        const uint64_t n = S->n;
+        S->d_C.ensure(n * (n - 1) / 2);
+        views.push_back(InstView{reinterpret_cast<const uint4 *>(S->d_bm.p), S->d_line_off.p, S->d_wshift.p,
+                                 S->d_order.p, S->d_C.p, S->n, 0});
+    }
+    DevBuf<InstView> d_views(views.size());
+    DevBuf<uint32_t> d_counter(1);
+    BM_CUDA(cudaMemcpyAsync(d_views.p, views.data(), views.size() * sizeof(InstView), cudaMemcpyHostToDevice, st));
+    PhaseEvents ev;
+    ev.create();
+    double rate[NUM_SHAPES];
+    double best = 0.0;
+    for (int s = 0; s < NUM_SHAPES; s++) {
+        std::vector<WorkUnit> units;
+        for (uint32_t v = 0; v < idx.size(); v++) {
+            std::vector<WorkUnit> u;
+            schedule_units(sets[idx[v]], (uint32_t)s + 1, nullptr, 0.0, &u);
+            for (auto &w : u) w.inst = v;
+            units.insert(units.end(), u.begin(), u.end());
+        }
+        sort_units(&units);
+        double padded = 0.0;
+        for (const auto &w : units) padded += (double)SHAPES[w.shape].TR * SHAPES[w.shape].TC * w.klen;
+        DevBuf<WorkUnit> d_units(units.size());
+        if (!units.empty())
+            BM_CUDA(cudaMemcpyAsync(d_units.p, units.data(), units.size() * sizeof(WorkUnit), cudaMemcpyHostToDevice, st));
+        BM_CUDA(cudaMemsetAsync(d_counter.p, 0, sizeof(uint32_t), st));
+        ev.record(0, st);
+        launch_compare(d_views.p, d_units.p, (uint32_t)units.size(), d_counter.p,
+                       std::min<uint32_t>((uint32_t)units.size(), (uint32_t)device_sms()), st);
+        ev.record(1, st);
+        BM_CUDA(cudaStreamSynchronize(st));
+        const double ms = ev.ms(0, 1);
+        rate[s] = ms > 0 ? padded / ms : 0.0;
+        best = std::max(best, rate[s]);
+    }
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        for (int s = 0; s < NUM_SHAPES; s++) g_tuned_eff[s] = best > 0 ? std::max(rate[s] / best, 1e-3) : 1.0;
+        g_tuned = true;
+        if (eff_out)
+            for (int s = 0; s < NUM_SHAPES; s++) eff_out[s] = g_tuned_eff[s];
+    }
+    {
+        std::lock_guard<std::mutex> lock(g_batch_mu);
+        g_plan.reset();  // units change: cached batch graphs are stale
+    }
+    for (uint32_t q = 0; q < k; q++) build_schedule(sets[q]);
+    BM_CUDA(cudaStreamSynchronize(st));
+}
+
 void release_batch_plan() {
     std::lock_guard<std::mutex> lock(g_batch_mu);
     g_plan.reset();

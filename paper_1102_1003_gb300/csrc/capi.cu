@@ -20,6 +20,7 @@ void build_set(batmap_set *S, const uint64_t *d_offsets, const uint32_t *d_tids,
 void enqueue_correct_compact(batmap_set *S, uint32_t *C, uint32_t s, uint32_t *d_pairs, uint64_t cap,
                              uint64_t *d_total, cudaStream_t st);
 void run_batch(batmap_set *const *sets, const uint32_t *s, uint32_t k, batmap_out *outs, cudaStream_t st);
+void autotune(batmap_set *const *sets, uint32_t k, double *eff_out, cudaStream_t st);
 void release_batch_plan();
 
 static std::atomic<uint64_t> g_gen{1};
@@ -236,6 +237,10 @@ batmap_status batmap_get_timing(const batmap_set *S, batmap_timing *t) {
 }
 
 uint64_t batmap_kernel_launches(void) { return g_launches.load(); }
+
+batmap_status batmap_autotune(batmap_set *const *sets, uint32_t k, double *shape_eff, cudaStream_t st) {
+    return guarded([&] { autotune(sets, k, shape_eff, st); });
+}
 
 batmap_status pair_support_batch(batmap_set *const *sets, const uint32_t *s, uint32_t k, batmap_out *outs,
                                  cudaStream_t st) {

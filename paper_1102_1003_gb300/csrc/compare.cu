@@ -472,9 +472,13 @@ void sort_units(std::vector<WorkUnit> *units) {
                      [](const WorkUnit &a, const WorkUnit &b) { return unit_cost(a) > unit_cost(b); });
 }
 
+bool tuned_shape_eff(double *eff);  // batch.cu
+
 void build_schedule(batmap_set *S) {
     S->units.clear();
-    schedule_units(S, S->params.tile, nullptr, 0.0, &S->units);
+    double eff[NUM_SHAPES];
+    const bool tuned = tuned_shape_eff(eff);
+    schedule_units(S, S->params.tile, tuned ? eff : nullptr, 0.0, &S->units);
     S->d_units.alloc(S->units.size());
     if (!S->units.empty())
         BM_CUDA(cudaMemcpyAsync(S->d_units.p, S->units.data(), S->units.size() * sizeof(WorkUnit),
