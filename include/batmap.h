@@ -210,6 +210,11 @@ typedef struct batmap_timing {
 /* Copy the phase durations of the set's most recent calls into *t. */
 batmap_status batmap_get_timing(const batmap_set *set, batmap_timing *t);
 
+/* Release the scratch the library caches between calls (the placement table
+ * of batmap_build, one uint32 per BatMap byte; the dense path's bitmap and
+ * workspace).  Call when no other call of the library is running. */
+void batmap_release_scratch(void);
+
 /* Number of kernels this library has launched in the process so far (a
  * diagnostic counter; differences around a region count its launches). */
 uint64_t batmap_kernel_launches(void);

@@ -28,7 +28,7 @@ EXPORTED = [
     "batmap_get_info", "batmap_export_layout", "pair_support_all", "pair_support_host",
     "pair_support_batch", "batmap_get_timing", "batmap_kernel_launches", "pair_threshold_noalloc",
     "pair_support_dense", "batmap_pool_create", "batmap_pool_free", "batmap_pool_info", "intersect_query",
-    "batmap_serve", "batmap_autotune",
+    "batmap_serve", "batmap_autotune", "batmap_release_scratch",
 ]
 
 
@@ -137,6 +137,8 @@ def load_library(path: str = LIB_PATH):
     L.batmap_serve.argtypes = [vp, vp, vp, vp, u32, ctypes.POINTER(batmap_serve_opts), vp, vp,
                                ctypes.POINTER(batmap_serve_stats), vp]
     L.batmap_serve.restype = ctypes.c_int
+    L.batmap_release_scratch.argtypes = []
+    L.batmap_release_scratch.restype = None
     L.batmap_autotune.argtypes = [ctypes.POINTER(vp), u32, ctypes.POINTER(ctypes.c_double), vp]
     L.batmap_autotune.restype = ctypes.c_int
     L.pair_threshold_noalloc.argtypes = [vp, u32, u32, vp, u64, ctypes.POINTER(u64), vp]
@@ -220,6 +222,11 @@ def batmap_get_timing(bset: BatMapSet) -> dict:
     t = batmap_timing()
     _check(load_library().batmap_get_timing(bset.handle, ctypes.byref(t)))
     return t.as_dict()
+
+
+def batmap_release_scratch():
+    """Free the scratch the library caches between calls."""
+    load_library().batmap_release_scratch()
 
 
 def batmap_kernel_launches() -> int:

@@ -11,6 +11,7 @@
 //   schedule  : compare work units (host, compare.cu)
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <numeric>
 
 #include "common.cuh"
@@ -133,19 +134,28 @@ __device__ __forceinline__ bool two_copies(uint32_t has) { return __popc(has) ==
 
 // Writes the two bytes of every element stored twice.  The indicator is 1 on
 // the copy whose twin sits in the cyclic predecessor table (Fig. 3).
+// Also counts the block's failed insertions into blocksums[block] (the count
+// pass of the ordered compaction that lists them).
 __global__ void k_finalize(ItemView v, const uint32_t *__restrict__ perm, uint32_t m,
                            uint32_t shift, const uint32_t *__restrict__ table,
-                           uint8_t *__restrict__ out) {
+                           uint8_t *__restrict__ out, uint64_t *__restrict__ blocksums) {
+    __shared__ uint32_t s_fail;
+    if (threadIdx.x == 0) s_fail = 0;
+    __syncthreads();
     uint32_t item;
     uint64_t e0, e1;
     chunk_range(v, blockIdx.x, &item, &e0, &e1);
     const uint64_t base = v.base[item];
     const uint32_t r = 1u << v.rlog[item];
+    uint32_t fails = 0;
     for (uint64_t e = e0 + threadIdx.x; e < e1; e += TPB) {
         uint32_t x = v.tids[e];
         if (x >= m) continue;
         Copies c = find_copies(x, base, r, shift, perm, m, table);
-        if (!two_copies(c.has)) continue;
+        if (!two_copies(c.has)) {
+            fails++;
+            continue;
+        }
 #pragma unroll
         for (uint32_t t = 0; t < 3; t++) {
             if (c.has & (1u << t)) {
@@ -155,6 +165,11 @@ __global__ void k_finalize(ItemView v, const uint32_t *__restrict__ perm, uint32
             }
         }
     }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) fails += __shfl_xor_sync(0xffffffffu, fails, d);
+    if ((threadIdx.x & 31) == 0 && fails) atomicAdd(&s_fail, fails);
+    __syncthreads();
+    if (threadIdx.x == 0) blocksums[blockIdx.x] = s_fail;
 }
 
 // ---- failed insertions, in (item, tid) order --------------------------------------
@@ -170,6 +185,7 @@ __global__ void k_failures(ItemView v, const uint32_t *__restrict__ perm, uint32
     const uint64_t base = v.base[item];
     const uint32_t r = 1u << v.rlog[item];
     uint64_t running = WRITE ? blocksums[blockIdx.x] : 0;
+    if (WRITE && blocksums[blockIdx.x + 1] == running) return;  // no failure in this block
     for (int j = 0; j < PER_THREAD; j++) {
         uint64_t e = e0 + (uint64_t)j * TPB + threadIdx.x;
         bool fail = false;
@@ -294,8 +310,26 @@ static unsigned grid_for(uint64_t work, unsigned tpb = 256) {
     return (unsigned)std::min<uint64_t>(std::max<uint64_t>(g, 1), 1u << 20);
 }
 
+// The placement scratch (one uint32 per BatMap byte) is kept between builds
+// so that repeated builds do not pay for allocating and freeing it; it is
+// released when a build needs less than a quarter of it or on
+// batmap_release_scratch().  Builds are serialised on it.
+static std::mutex g_scratch_mu;
+static DevBuf<uint32_t> g_scratch;
+
+static DevBuf<uint32_t> &scratch_table(uint64_t slots) {
+    if (g_scratch.n < slots || g_scratch.n > 4 * slots + (1u << 20)) g_scratch.alloc(slots);
+    return g_scratch;
+}
+
+void release_scratch() {
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    g_scratch.release();
+}
+
 void build_set(batmap_set *S, const uint64_t *d_offsets, const uint32_t *d_tids,
                const uint32_t *d_perm) {
+    std::lock_guard<std::mutex> scratch_lock(g_scratch_mu);
     const uint32_t m = S->m, n = S->n;
     cudaStream_t st = S->stream;
     const batmap_params &P = S->params;
@@ -421,21 +455,19 @@ void build_set(batmap_set *S, const uint64_t *d_offsets, const uint32_t *d_tids,
 
     // ---- place + finalize ----
     {
-        DevBuf<uint32_t> table(S->bytes);
-        BM_CUDA(cudaMemsetAsync(table.p, 0xFF, table.bytes(), st));
+        DevBuf<uint32_t> &table = scratch_table(S->bytes);
+        BM_CUDA(cudaMemsetAsync(table.p, 0xFF, S->bytes * sizeof(uint32_t), st));
         const uint32_t max_moves = 3u * std::max<uint32_t>(P.max_loop, 1u);
         E.record(2, st);
         k_place<<<2u * nch, TPB, 0, st>>>(v, d_perm, m, S->shift, max_moves, table.p);
         BM_CHECK_LAUNCH();
         E.record(3, st);
-        k_finalize<<<nch, TPB, 0, st>>>(v, d_perm, m, S->shift, table.p, S->d_bm.p);
-        BM_CHECK_LAUNCH();
-
-        // failed insertions, ordered by (item, tid)
+        // failed insertions, ordered by (item, tid): counted by finalize, listed below
         DevBuf<uint64_t> bs(nch + 1), d_tot(1);
-        k_failures<false><<<nch, TPB, 0, st>>>(v, d_perm, m, S->shift, table.p, bs.p, nullptr, nullptr);
+        k_finalize<<<nch, TPB, 0, st>>>(v, d_perm, m, S->shift, table.p, S->d_bm.p, bs.p);
         BM_CHECK_LAUNCH();
-        scan_exclusive(bs.p, nch, d_tot.p, st);
+        k_scan_single_block<<<1, SCAN_TPB, 0, st>>>(bs.p, nch, d_tot.p, 1);
+        BM_CHECK_LAUNCH();
         uint64_t nfail = 0;
         BM_CUDA(cudaMemcpyAsync(&nfail, d_tot.p, 8, cudaMemcpyDeviceToHost, st));
         BM_CUDA(cudaStreamSynchronize(st));
@@ -449,7 +481,6 @@ void build_set(batmap_set *S, const uint64_t *d_offsets, const uint32_t *d_tids,
         }
         k_fail_offsets<<<(n + 1 + 255) / 256, 256, 0, st>>>(f_item.p, nfail, n, S->d_fail_off.p);
         BM_CHECK_LAUNCH();
-        table.release();
 
         // ---- correction entries ----
         S->n_corr = 0;

@@ -21,6 +21,8 @@ void enqueue_correct_compact(batmap_set *S, uint32_t *C, uint32_t s, uint32_t *d
                              uint64_t *d_total, cudaStream_t st);
 void run_batch(batmap_set *const *sets, const uint32_t *s, uint32_t k, batmap_out *outs, cudaStream_t st);
 void autotune(batmap_set *const *sets, uint32_t k, double *eff_out, cudaStream_t st);
+void release_scratch();
+void release_dense_workspace();
 void release_batch_plan();
 
 static std::atomic<uint64_t> g_gen{1};
@@ -237,6 +239,11 @@ batmap_status batmap_get_timing(const batmap_set *S, batmap_timing *t) {
 }
 
 uint64_t batmap_kernel_launches(void) { return g_launches.load(); }
+
+void batmap_release_scratch(void) {
+    release_scratch();
+    release_dense_workspace();
+}
 
 batmap_status batmap_autotune(batmap_set *const *sets, uint32_t k, double *shape_eff, cudaStream_t st) {
     return guarded([&] { autotune(sets, k, shape_eff, st); });

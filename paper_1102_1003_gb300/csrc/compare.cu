@@ -213,15 +213,19 @@ __device__ __forceinline__ void process_unit(uint4 *smem, const InstView &V, con
     }
 }
 
-// Register-streaming variant: every thread loads its own 8 row words and MC
-// column words per 4-word step straight from global memory (128-bit loads
-// through L1; lanes of a warp that share a row or a column are served by one
-// request) and prefetches the next step while comparing the current one.
-// No shared memory and no barrier: suited to narrow column tiles, where a
-// loaded row word has only a few partners and staging costs more than it
-// saves.  The wrap of a narrower row is an incremental index reset.
+// Register-streaming variant: every thread streams its own 8 row chunks per
+// 4-word step into a private 4-deep shared-memory ring with cp.async (it
+// waits only for its own copy groups: no block barrier) and loads its MC
+// column words straight from global memory (128-bit loads through L1; lanes
+// that share a column are served by one request).  Suited to narrow column
+// tiles, where a staged row word has only a few partners.  The wrap of a
+// narrower row is an incremental index reset.
+// Per-thread ring depth of the register-streaming path (16-byte row chunks
+// prefetched DEPTH-1 steps ahead).
+constexpr int DIRECT_DEPTH = 4;
+
 template <int TR_T, int TC_T, int MC>
-__device__ __forceinline__ void process_unit_direct(const InstView &V, const WorkUnit &wu) {
+__device__ __forceinline__ void process_unit_direct(uint4 *smem, const InstView &V, const WorkUnit &wu) {
     const int tid = threadIdx.x;
     const int tc = tid % TC_T;
     const int tr = tid / TC_T;
@@ -259,28 +263,43 @@ __device__ __forceinline__ void process_unit_direct(const InstView &V, const Wor
 #pragma unroll
         for (int b = 0; b < MC; b++) acc[a][b] = 0;
 
-    auto load_rows = [&](uint4 (&X)[8]) {
+    // Each thread copies its own row chunks into a private ring slot
+    // ring[(step % DEPTH) * 8 + a][tid] and waits only for its own copy groups.
+    auto issue_rows = [&](uint32_t step) {
+        uint4 *slot = smem + (size_t)(step % DIRECT_DEPTH) * 8 * 256 + tid;
 #pragma unroll
         for (int a = 0; a < 8; a++) {
-            X[a] = rbase[a] != 0xFFFFFFFFu ? __ldg(bm + (size_t)rbase[a] + rcur[a]) : zero;
+            const bool ok = rbase[a] != 0xFFFFFFFFu;
+            cp_async16(smem_u32(slot + a * 256), ok ? (const void *)(bm + (size_t)rbase[a] + rcur[a]) : (const void *)bm,
+                       ok);
             rcur[a] = (rcur[a] + 1 == rlen[a]) ? 0 : rcur[a] + 1;
         }
     };
+#pragma unroll
+    for (int d = 0; d < DIRECT_DEPTH - 1; d++) {
+        if ((uint32_t)d < nq) issue_rows(d);
+        cp_async_commit();
+    }
 
-    uint4 X[8];
-    load_rows(X);
+    // column chunks are loaded one step ahead into registers
+    uint4 Y[MC];
+#pragma unroll
+    for (int b = 0; b < MC; b++) Y[b] = (cbase[b] != 0xFFFFFFFFu && nq) ? __ldg(bm + (size_t)cbase[b]) : zero;
+
 #pragma unroll 1
     for (uint32_t q = 0; q < nq; q++) {
-        uint4 Y[MC];
+        if (q + DIRECT_DEPTH - 1 < nq) issue_rows(q + DIRECT_DEPTH - 1);
+        cp_async_commit();
+        uint4 Yn[MC];
+        const bool more = q + 1 < nq;
 #pragma unroll
-        for (int b = 0; b < MC; b++) Y[b] = cbase[b] != 0xFFFFFFFFu ? __ldg(bm + (size_t)cbase[b] + q) : zero;
-        uint4 Xn[8];
-        if (q + 1 < nq) {
-            load_rows(Xn);
-        } else {
+        for (int b = 0; b < MC; b++)
+            Yn[b] = (more && cbase[b] != 0xFFFFFFFFu) ? __ldg(bm + (size_t)cbase[b] + q + 1) : zero;
+        cp_async_wait<DIRECT_DEPTH - 1>();
+        uint4 X[8];
+        const uint4 *slot = smem + (size_t)(q % DIRECT_DEPTH) * 8 * 256 + tid;
 #pragma unroll
-            for (int a = 0; a < 8; a++) Xn[a] = zero;
-        }
+        for (int a = 0; a < 8; a++) X[a] = slot[a * 256];
 #pragma unroll
         for (int kk = 0; kk < 4; kk++) {
             uint32_t yw[MC], yi[MC];
@@ -298,8 +317,9 @@ __device__ __forceinline__ void process_unit_direct(const InstView &V, const Wor
             }
         }
 #pragma unroll
-        for (int a = 0; a < 8; a++) X[a] = Xn[a];
+        for (int b = 0; b < MC; b++) Y[b] = Yn[b];
     }
+    cp_async_wait<0>();
 
     const uint64_t n = V.n;
 #pragma unroll
@@ -344,7 +364,7 @@ size_t compare_smem_bytes(uint32_t shape_idx) {
 }
 
 static size_t max_smem_bytes() {
-    size_t m = 0;
+    size_t m = (size_t)DIRECT_DEPTH * 8 * 256 * sizeof(uint4);  // register-streaming ring
     for (uint32_t s = 0; s < NUM_SHAPES; s++) m = std::max(m, compare_smem_bytes(s));
     return m;
 }
@@ -368,7 +388,7 @@ k_compare(const InstView *__restrict__ views, const WorkUnit *__restrict__ units
 #define X(i, a, b, c, d, e) case i: process_unit<a, b, c, d, e>(smem, V, wu); break;
             BM_SHAPE_LIST(X)
 #undef X
-#define X(i, a, b, c) case i: process_unit_direct<a, b, c>(V, wu); break;
+#define X(i, a, b, c) case i: process_unit_direct<a, b, c>(smem, V, wu); break;
             BM_DIRECT_LIST(X)
 #undef X
             default: break;

@@ -299,6 +299,12 @@ struct DenseWork {
 static std::mutex g_dense_mu;
 static DenseWork *g_dense = nullptr;
 
+void release_dense_workspace() {
+    std::lock_guard<std::mutex> lock(g_dense_mu);
+    delete g_dense;
+    g_dense = nullptr;
+}
+
 void run_dense(uint32_t m, uint32_t n, const uint64_t *d_off, const uint32_t *d_tids, uint32_t s,
                uint32_t *d_pairs, uint64_t cap, uint64_t *n_out, uint32_t *d_full, batmap_timing *tout,
                cudaStream_t st) {
