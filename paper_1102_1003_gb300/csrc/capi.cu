@@ -90,7 +90,7 @@ batmap_status batmap_build(const batmap_params *p, uint32_t m, uint32_t n, const
         BM_REQUIRE(P.load_num >= 1 && P.load_den >= 1 && P.load_num <= 16 * P.load_den,
                    BATMAP_ERR_ARG, "load factor must be in [1/load_den, 16]");
         BM_REQUIRE(P.min_shift >= 7 && P.min_shift <= 24, BATMAP_ERR_ARG, "min_shift must be in [7, 24]");
-        BM_REQUIRE(P.tile <= NUM_SHAPES, BATMAP_ERR_ARG, "tile must be 0..12");
+        BM_REQUIRE(P.tile <= NUM_SHAPES, BATMAP_ERR_ARG, "tile must be 0..13");
         BM_REQUIRE(P.max_loop >= 1 && P.max_loop <= (1u << 20), BATMAP_ERR_ARG, "max_loop out of range");
         batmap_set *S = new batmap_set();
         S->params = P;

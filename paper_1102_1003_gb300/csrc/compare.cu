@@ -42,6 +42,7 @@ const ShapeDesc SHAPES[NUM_SHAPES] = {
     {7, 128, 128, 8, 4, 0, 0.90},   {8, 256, 64, 8, 4, 0, 0.90},
     {9, 512, 32, 8, 4, 0, 0.88},    {10, 1024, 16, 8, 4, 0, 0.86},
     {11, 2048, 8, 8, 4, 0, 0.84},   {12, 2048, 4, 4, 4, 0, 0.70},
+    {13, 1024, 12, 12, 4, 0, 0.86},
 };
 
 int device_sms() {
@@ -224,7 +225,7 @@ __device__ __forceinline__ void process_unit(uint4 *smem, const InstView &V, con
 // prefetched DEPTH-1 steps ahead).
 constexpr int DIRECT_DEPTH = 4;
 
-template <int TR_T, int TC_T, int MC>
+template <int TR_T, int TC_T, int MC, int MR = 8>
 __device__ __forceinline__ void process_unit_direct(uint4 *smem, const InstView &V, const WorkUnit &wu) {
     const int tid = threadIdx.x;
     const int tc = tid % TC_T;
@@ -235,9 +236,9 @@ __device__ __forceinline__ void process_unit_direct(uint4 *smem, const InstView 
     const uint4 *__restrict__ bm = V.bm;
 
     // row state: chunk index of the row start, current chunk, row length (chunks)
-    uint32_t rbase[8], rcur[8], rlen[8];
+    uint32_t rbase[MR], rcur[MR], rlen[MR];
 #pragma unroll
-    for (int a = 0; a < 8; a++) {
+    for (int a = 0; a < MR; a++) {
         const uint32_t g = wu.r0 + tr + TR_T * a;
         if (g < wu.r1) {
             const uint32_t e = __ldg(&V.wshift[g]);
@@ -257,18 +258,18 @@ __device__ __forceinline__ void process_unit_direct(uint4 *smem, const InstView 
         cbase[b] = g < wu.c1 ? __ldg(&V.line_off[g]) * 8u + q0 : 0xFFFFFFFFu;
     }
 
-    uint32_t acc[8][MC];
+    uint32_t acc[MR][MC];
 #pragma unroll
-    for (int a = 0; a < 8; a++)
+    for (int a = 0; a < MR; a++)
 #pragma unroll
         for (int b = 0; b < MC; b++) acc[a][b] = 0;
 
     // Each thread copies its own row chunks into a private ring slot
-    // ring[(step % DEPTH) * 8 + a][tid] and waits only for its own copy groups.
+    // ring[(step % DEPTH) * MR + a][tid] and waits only for its own copy groups.
     auto issue_rows = [&](uint32_t step) {
-        uint4 *slot = smem + (size_t)(step % DIRECT_DEPTH) * 8 * 256 + tid;
+        uint4 *slot = smem + (size_t)(step % DIRECT_DEPTH) * MR * 256 + tid;
 #pragma unroll
-        for (int a = 0; a < 8; a++) {
+        for (int a = 0; a < MR; a++) {
             const bool ok = rbase[a] != 0xFFFFFFFFu;
             cp_async16(smem_u32(slot + a * 256), ok ? (const void *)(bm + (size_t)rbase[a] + rcur[a]) : (const void *)bm,
                        ok);
@@ -296,10 +297,10 @@ __device__ __forceinline__ void process_unit_direct(uint4 *smem, const InstView 
         for (int b = 0; b < MC; b++)
             Yn[b] = (more && cbase[b] != 0xFFFFFFFFu) ? __ldg(bm + (size_t)cbase[b] + q + 1) : zero;
         cp_async_wait<DIRECT_DEPTH - 1>();
-        uint4 X[8];
-        const uint4 *slot = smem + (size_t)(q % DIRECT_DEPTH) * 8 * 256 + tid;
+        uint4 X[MR];
+        const uint4 *slot = smem + (size_t)(q % DIRECT_DEPTH) * MR * 256 + tid;
 #pragma unroll
-        for (int a = 0; a < 8; a++) X[a] = slot[a * 256];
+        for (int a = 0; a < MR; a++) X[a] = slot[a * 256];
 #pragma unroll
         for (int kk = 0; kk < 4; kk++) {
             uint32_t yw[MC], yi[MC];
@@ -309,7 +310,7 @@ __device__ __forceinline__ void process_unit_direct(uint4 *smem, const InstView 
                 yi[b] = yw[b] & 0x80808080u;
             }
 #pragma unroll
-            for (int a = 0; a < 8; a++) {
+            for (int a = 0; a < MR; a++) {
                 const uint32_t xw = lane_word(X[a], kk);
                 const uint32_t xi = xw & 0x80808080u;
 #pragma unroll
@@ -323,7 +324,7 @@ __device__ __forceinline__ void process_unit_direct(uint4 *smem, const InstView 
 
     const uint64_t n = V.n;
 #pragma unroll
-    for (int a = 0; a < 8; a++) {
+    for (int a = 0; a < MR; a++) {
         const uint32_t gi = wu.r0 + tr + TR_T * a;
         if (gi >= wu.r1) continue;
         const uint32_t oi = __ldg(&V.order[gi]);
@@ -349,12 +350,13 @@ __device__ __forceinline__ void process_unit_direct(uint4 *smem, const InstView 
     X(5, 256, 1, 4, 8, 2)
 
 #define BM_DIRECT_LIST(X) \
-    X(6, 16, 16, 8)         \
-    X(7, 32, 8, 8)          \
-    X(8, 64, 4, 8)          \
-    X(9, 128, 2, 8)         \
-    X(10, 256, 1, 8)        \
-    X(11, 256, 1, 4)
+    X(6, 16, 16, 8, 8)      \
+    X(7, 32, 8, 8, 8)       \
+    X(8, 64, 4, 8, 8)       \
+    X(9, 128, 2, 8, 8)      \
+    X(10, 256, 1, 8, 8)     \
+    X(11, 256, 1, 4, 8)     \
+    X(12, 256, 1, 12, 4)
 
 size_t compare_smem_bytes(uint32_t shape_idx) {
 #define X(i, a, b, c, d, e) if (shape_idx == i) return Tile<a, b, c, d, e>::SMEM;
@@ -388,7 +390,7 @@ k_compare(const InstView *__restrict__ views, const WorkUnit *__restrict__ units
 #define X(i, a, b, c, d, e) case i: process_unit<a, b, c, d, e>(smem, V, wu); break;
             BM_SHAPE_LIST(X)
 #undef X
-#define X(i, a, b, c) case i: process_unit_direct<a, b, c>(smem, V, wu); break;
+#define X(i, a, b, c, d) case i: process_unit_direct<a, b, c, d>(smem, V, wu); break;
             BM_DIRECT_LIST(X)
 #undef X
             default: break;

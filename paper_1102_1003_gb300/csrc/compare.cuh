@@ -12,11 +12,11 @@ namespace bm {
 // memory; direct shapes (stages == 0) stream 4-word steps into registers.
 struct ShapeDesc {
     uint32_t id;   // 1-based; 0 = automatic
-    uint32_t TR, TC, MC, KC, stages;
+    uint32_t TR, TC, MC, KC, stages;  // (MC: columns per thread)
     double eff;    // relative throughput per padded word-pair (scheduler prior)
 };
 
-constexpr int NUM_SHAPES = 12;
+constexpr int NUM_SHAPES = 13;
 extern const ShapeDesc SHAPES[NUM_SHAPES];
 
 // Number of SMs of the current device (cached).
