@@ -117,6 +117,17 @@ def _traffic_record():
     return rec
 
 
+def max_over_ranks(value: float, device=None) -> float:
+    """The job's time is the slowest rank's: all-reduce(MAX) across the process group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _sample_pairs(n, k, seed):
     rng = np.random.default_rng(seed)
     i = rng.integers(0, n, k)
@@ -268,9 +279,7 @@ def run_mine(args, inst, rank, world):
     launches = L.batmap_kernel_launches() - launches0
     elapsed = ev0.elapsed_time(ev1) / 1e3
     if dist:
-        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+        elapsed = max_over_ranks(elapsed, dev)
         dist.barrier()
     clocks = sampler.stop()
     assert got == n_out

@@ -226,3 +226,35 @@ def test_config2_full_scale_exact():
     _check_exact(inst, full, n_out, pairs)
     info = bset.info
     assert info["n_classes"] >= 6
+
+
+@pytest.mark.parametrize("name", ["cfg4_0.1", "cfg4_1", "cfg4_5"])
+def test_config4_full_scale_sampled(name):
+    """Configuration 4 at full size (m = 4,194,304, n = 8,192, 33.5M pairs) in
+    the bench's launch configuration: 3000 sampled supports against the merge
+    oracle, whole rows through the row-sum invariant, and the frequent-pair
+    list against the supports."""
+    inst = datagen.config_instance(name)
+    full, n_out, pairs, bset = run_all_pairs(inst, perm_seed=4)
+    n = inst.n
+    rng = np.random.default_rng(12)
+    ii = rng.integers(0, n - 1, 3000)
+    jj = ii + 1 + (rng.integers(0, n, 3000) % (n - 1 - ii))
+    ref = oracle.pairs_list(inst.offsets, inst.tids, ii, jj, threads=THREADS)
+    idx = oracle.packed_index(n, ii, jj)
+    assert np.array_equal(full[idx], ref)
+    # sum over partners of row i = sum over x in S_i of (|T_x| - 1)
+    tlen = np.bincount(inst.tids, minlength=inst.m).astype(np.int64)
+    for i in rng.integers(0, n, 12):
+        i = int(i)
+        cols = np.arange(n)
+        lo, hi = np.minimum(i, cols), np.maximum(i, cols)
+        keep = cols != i
+        row = full[oracle.packed_index(n, lo[keep], hi[keep])].astype(np.int64).sum()
+        assert row == (tlen[inst.tidlist(i)] - 1).sum()
+    # the frequent pairs are exactly the supports >= s, lexicographic
+    assert n_out == int((full >= inst.s).sum())
+    if n_out:
+        key = pairs[:, 0].astype(np.int64) * n + pairs[:, 1]
+        assert (np.diff(key) > 0).all() and (pairs[:, 0] < pairs[:, 1]).all()
+        assert np.array_equal(full[oracle.packed_index(n, pairs[:, 0], pairs[:, 1])], pairs[:, 2])
