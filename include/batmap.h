@@ -302,15 +302,16 @@ batmap_status batmap_serve(const batmap_pool *pool, const uint32_t *h_qoff, cons
 /*
  * Dense-bitmap comparison path (Sec. I-B: the bitmap vertical representation,
  * m*n bits, where a support is AND + popcount).  Builds the item x transaction
- * bitmap as bf16 {0, 1} and computes all supports as the dense contraction
- * M M^T on the tensor cores (tcgen05, FP32 accumulation in tensor memory,
- * exact because every partial sum is an integer below 2^24), then the same
- * threshold compaction as pair_support_all.
+ * bitmap as e4m3 {0, 1} bytes and computes all supports as the dense
+ * contraction M M^T on the tensor cores (tcgen05 kind::f8f6f4, FP32
+ * accumulation in tensor memory, exact because every product is 0 or 1 and
+ * every partial sum an integer below 2^24), then the same threshold
+ * compaction as pair_support_all.
  *   m, n, d_offsets, d_tids : CSR tidlists as in batmap_build (1 <= m <= 2^24).
  *   s, d_pairs, cap, n_out, d_full : as in pair_support_all.
  *   timing  : optional host struct; build_ms = bitmap build, compare_ms = the
  *             tensor-core kernel, compact_ms = compaction.
- * The bitmap (n x ceil(m/64)*64 bf16 values) and scratch are cached inside
+ * The bitmap (n x ceil(m/128)*128 bytes) and scratch are cached inside
  * the library between calls.  Synchronises the stream.
  */
 batmap_status pair_support_dense(uint32_t m, uint32_t n, const uint64_t *d_offsets, const uint32_t *d_tids,

@@ -3,19 +3,20 @@
 // bitmaps is the dense boolean contraction C = M M^T with M in {0,1}^(n x m)
 // (items x transactions), so it runs on the 5th-generation tensor cores:
 //
-//   * M is materialised as bf16 {0, 1} (row = item, K = transactions,
-//     K-major, rows padded to a multiple of 64 elements);
-//   * TMA loads 128 x 64 (A) and 256 x 64 (B) tiles into 128-byte-swizzled
-//     shared memory through a 4-stage mbarrier ring;
-//   * one thread issues tcgen05.mma.cta_group::1.kind::f16 (M = 128,
-//     N = 256, K = 16) into an FP32 accumulator in tensor memory;
+//   * M is materialised as e4m3 {0, 1} bytes (1.0 = 0x38; row = item,
+//     K = transactions, K-major, rows padded to a multiple of 128);
+//   * TMA loads 128 x 128 (A) and 256 x 128 (B) byte tiles into
+//     128-byte-swizzled shared memory through a 4-stage mbarrier ring;
+//   * one thread issues tcgen05.mma.cta_group::1.kind::f8f6f4 (M = 128,
+//     N = 256, K = 32) into an FP32 accumulator in tensor memory;
 //   * four epilogue warps read the accumulator with tcgen05.ld, convert to
 //     integers and add them into the packed upper triangle.
 //
-// Exactness: every product is 0 or 1 and every partial sum an integer below
-// 2^24, which FP32 represents exactly; INT8 MMA (kind::i8) is not available on
-// sm_103a.  Split-K partial sums are added with integer atomics (exact in any
-// order).  Only tiles that hold a pair i < j are computed.
+// Exactness: every product is exactly 0 or 1 and every partial sum an integer
+// below 2^24, which the FP32 accumulator represents exactly (the tests check
+// bit-exactness at supports up to 10^6); INT8 MMA (kind::i8) is not available
+// on sm_103a.  Split-K partial sums are added with integer atomics (exact in
+// any order).  Only tiles that hold a pair i < j are computed.
 //
 // Every mbarrier wait is bounded; on timeout the kernel records an error
 // flag, stops issuing work, waits (bounded) for what it issued, frees its
@@ -36,11 +37,11 @@ void enqueue_threshold(uint32_t *C, uint64_t n, uint32_t s, uint32_t *d_pairs, u
 
 namespace dense {
 
-constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4, UMMA_K = 16;
-constexpr uint32_t A_BYTES = BM * BK * 2;          // 16 KiB
-constexpr uint32_t B_BYTES = BN * BK * 2;          // 32 KiB
+constexpr int BM = 128, BN = 256, BK = 128, STAGES = 4, UMMA_K = 32;
+constexpr uint32_t A_BYTES = BM * BK;          // 16 KiB
+constexpr uint32_t B_BYTES = BN * BK;          // 32 KiB
 constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr uint32_t TMEM_COLS = 256;                // FP32 accumulator 128 lanes x 256 columns
+constexpr uint32_t TMEM_COLS = 256;            // FP32 accumulator 128 lanes x 256 columns
 constexpr int THREADS = 192;                       // warp 0 TMA, warp 1 MMA, warps 2..5 epilogue
 constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
 constexpr uint32_t SPIN_LIMIT = 1u << 26;          // bounded waits (tens of ms per wait)
@@ -92,14 +93,14 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
     return d;
 }
 
-// Instruction descriptor: D = F32, A = B = BF16, both K-major, M = 128, N = 256.
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+// Instruction descriptor: D = F32, A = B = E4M3, both K-major, M = 128, N = 256.
+constexpr uint32_t IDESC = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(BN >> 3) << 17) |
                            ((uint32_t)(BM >> 4) << 24);
 
 __device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t accumulate) {
     asm volatile(
         "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n"
         ::"r"(tmem_d), "l"(da), "l"(db), "r"(IDESC), "r"(accumulate));
 }
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
@@ -172,7 +173,7 @@ k_dense_mmt(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             const uint64_t da = smem_desc(a0), db = smem_desc(a0 + A_BYTES);
 #pragma unroll
             for (int k = 0; k < BK / UMMA_K; k++) {
-                // advance 16 bf16 = 32 bytes along K inside the swizzled 128-byte rows
+                // advance 32 e4m3 = 32 bytes along K inside the swizzled 128-byte rows
                 umma_bf16(tmem, da + (uint64_t)(k * 2), db + (uint64_t)(k * 2), (it > 0 || k > 0) ? 1u : 0u);
             }
             umma_commit(smem_addr(&bars[STAGES + st]));  // frees the stage when the MMAs have read it
@@ -234,9 +235,9 @@ k_dense_mmt(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     }
 }
 
-// Scatter the tidlists into the zeroed bf16 bitmap (1.0 = 0x3F80).
+// Scatter the tidlists into the zeroed e4m3 bitmap (1.0 = 0x38).
 __global__ void k_bitmap(const uint64_t *__restrict__ off, const uint32_t *__restrict__ tids, uint32_t n,
-                         uint32_t m, uint64_t ld, uint16_t *__restrict__ M, int *__restrict__ err) {
+                         uint32_t m, uint64_t ld, uint8_t *__restrict__ M, int *__restrict__ err) {
     const uint32_t i = blockIdx.y;
     if (i >= n) return;
     const uint64_t b = off[i], e = off[i + 1];
@@ -247,7 +248,7 @@ __global__ void k_bitmap(const uint64_t *__restrict__ off, const uint32_t *__res
             atomicExch(err, 2);
             continue;
         }
-        M[(uint64_t)i * ld + x] = 0x3F80;
+        M[(uint64_t)i * ld + x] = 0x38;
     }
 }
 
@@ -273,10 +274,10 @@ static CUtensorMap make_map(void *base, uint64_t rows, uint64_t cols_elems, uint
     CUtensorMap map;
     std::memset(&map, 0, sizeof(map));
     cuuint64_t dims[2] = {cols_elems, rows};
-    cuuint64_t strides[1] = {cols_elems * 2};
+    cuuint64_t strides[1] = {cols_elems};
     cuuint32_t box[2] = {(cuuint32_t)BK, box_rows};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = encode_fn()(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
+    CUresult r = encode_fn()(&map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, base, dims, strides, box, estr,
                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     BM_REQUIRE(r == CUDA_SUCCESS, BATMAP_ERR_CUDA, "cuTensorMapEncodeTiled failed");
@@ -287,7 +288,7 @@ static CUtensorMap make_map(void *base, uint64_t rows, uint64_t cols_elems, uint
 
 // Workspace kept across calls (bitmap, supports, tile list, scratch).
 struct DenseWork {
-    DevBuf<uint16_t> bitmap;
+    DevBuf<uint8_t> bitmap;
     DevBuf<uint32_t> C;
     DevBuf<dense::Tile> tiles;
     DevBuf<int> err;
@@ -329,7 +330,7 @@ void run_dense(uint32_t m, uint32_t n, const uint64_t *d_off, const uint32_t *d_
     W.err.ensure(1);
     BM_CUDA(cudaMemsetAsync(W.err.p, 0, sizeof(int), st));
     W.bitmap.ensure(nrows * ld);
-    BM_CUDA(cudaMemsetAsync(W.bitmap.p, 0, nrows * ld * 2, st));
+    BM_CUDA(cudaMemsetAsync(W.bitmap.p, 0, nrows * ld, st));
     if (n) {
         dim3 grid((unsigned)std::min<uint64_t>((m + 255) / 256, 64), n);
         k_bitmap<<<grid, 256, 0, st>>>(d_off, d_tids, n, m, ld, W.bitmap.p, W.err.p);

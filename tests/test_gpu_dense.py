@@ -69,3 +69,25 @@ def test_dense_config2_full_scale_exact():
     20-bit integers exactly."""
     inst = datagen.config_instance("cfg2")
     _check(inst)
+
+
+@pytest.mark.parametrize("name", ["cfg4_1", "cfg4_5"])
+def test_dense_config4_full_scale_sampled(name):
+    """Configuration 4 at full size on the tensor-core path: sampled supports
+    against the merge oracle and whole rows through the row-sum invariant."""
+    inst = datagen.config_instance(name)
+    full, n_out, pairs, _ = _dense(inst)
+    n = inst.n
+    rng = np.random.default_rng(21)
+    ii = rng.integers(0, n - 1, 2000)
+    jj = ii + 1 + (rng.integers(0, n, 2000) % (n - 1 - ii))
+    ref = oracle.pairs_list(inst.offsets, inst.tids, ii, jj, threads=THREADS)
+    assert np.array_equal(full[oracle.packed_index(n, ii, jj)], ref)
+    tlen = np.bincount(inst.tids, minlength=inst.m).astype(np.int64)
+    for i in rng.integers(0, n, 8):
+        i = int(i)
+        cols = np.arange(n)
+        keep = cols != i
+        lo, hi = np.minimum(i, cols)[keep], np.maximum(i, cols)[keep]
+        assert full[oracle.packed_index(n, lo, hi)].astype(np.int64).sum() == (tlen[inst.tidlist(i)] - 1).sum()
+    assert n_out == int((full >= inst.s).sum())
