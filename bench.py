@@ -431,6 +431,54 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def run_nsweep(args):
+    """Sec. IV-A / Fig. 5 shape: all pair supports at a constant instance size of
+    10^7 items and 5% density for a growing number of distinct items n."""
+    import torch
+    import paper_1102_1003_gb300 as pkg
+    import oracle
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    rows = []
+    for n in args.nsweep:
+        inst = datagen.nsweep_instance(n)
+        off = torch.from_numpy(inst.offsets.view(np.int64)).to(dev)
+        tids = torch.from_numpy(inst.tids.view(np.int32)).to(dev)
+        perm = torch.from_numpy(datagen.permutations(inst.m, 3).view(np.int32)).to(dev)
+        npairs = n * (n - 1) // 2
+        full = torch.empty(npairs, dtype=torch.int32, device=dev)
+        nopairs = torch.empty((1, 3), dtype=torch.int32, device=dev)
+        times = []
+        for rep in range(1 + args.steps):
+            t0 = time.perf_counter()
+            b = pkg.batmap_build(inst.m, off, tids, perm)
+            pkg.pair_support_all(b, 2**32 - 1, pairs=nopairs, full=full)  # every support, no list
+            torch.cuda.synchronize()
+            if rep:
+                times.append((time.perf_counter() - t0, pkg.batmap_get_timing(b)))
+            info = b.info
+            b.free()
+        rng = np.random.default_rng(n)
+        ii = rng.integers(0, n - 1, 500)
+        jj = ii + 1 + (rng.integers(0, n, 500) % (n - 1 - ii))
+        ref = oracle.pairs_list(inst.offsets, inst.tids, ii, jj, threads=os.cpu_count() or 4)
+        got = full.cpu().numpy()[oracle.packed_index(n, ii, jj)].astype(np.uint32)
+        wall = statistics.mean(t for t, _ in times)
+        rows.append({"n": n, "m": inst.m, "tids": int(inst.tids.size), "pairs": npairs,
+                     "batmap_bytes": int(info["bytes"]), "step_ms": 1e3 * wall,
+                     "build_ms": statistics.mean(t["build_ms"] for _, t in times),
+                     "compare_ms": statistics.mean(t["compare_ms"] for _, t in times),
+                     "pair_supports_per_s": npairs / wall,
+                     "logical_GBps": 8.0 * info["word_pairs"] / (statistics.mean(t["compare_ms"] for _, t in times) / 1e3) / 1e9,
+                     "sampled_exact": bool(np.array_equal(got, ref))})
+        del full, off, tids, perm
+        pkg.batmap_release_scratch()
+        torch.cuda.empty_cache()
+    print(json.dumps({"metric": METRIC, "workload": "nsweep", "unit": UNIT,
+                      "config": "10^7 items, density 5%, m = 10^7 / (0.05 n) (Sec. IV-A, Fig. 5 shape)",
+                      "rows": rows}), flush=True)
+
+
 def run_serve(args):
     """Serving workload: pool of sets over 2^26 with Zipf sizes on [10, 1e6],
     Poisson-arriving queries (80% pairs, 20% 3..8-way), continuous batching."""
@@ -515,7 +563,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["mine", "reference"], default="mine")
-    ap.add_argument("--workload", choices=sorted(WORKLOAD_DESC) + ["serve", "batch"], default="cfg2")
+    ap.add_argument("--workload", choices=sorted(WORKLOAD_DESC) + ["serve", "batch", "nsweep"], default="cfg2")
+    ap.add_argument("--nsweep", type=int, nargs="+", default=[1000, 2000, 4000, 8000, 16000, 32000, 64000])
     ap.add_argument("--instances", type=int, default=64, help="instances (batch workload)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--pool-sets", type=int, default=100_000, help="serving pool size (serve workload)")
@@ -528,9 +577,9 @@ def main():
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
-    if args.workload in ("serve", "batch"):
+    if args.workload in ("serve", "batch", "nsweep"):
         if rank == 0:
-            (run_serve if args.workload == "serve" else run_batch)(args)
+            {"serve": run_serve, "batch": run_batch, "nsweep": run_nsweep}[args.workload](args)
         return
     inst = datagen.config_instance(args.workload)
     if args.impl == "reference":

@@ -162,6 +162,14 @@ def config_instance(name: str, scale_n: int | None = None) -> Instance:
     return zipf_tidlists(c["m"], n, c["density"], c["seed"], 1.0, c["s"], name)
 
 
+def nsweep_instance(n: int, total: int = 10_000_000, density: float = 0.05, seed: int = 7) -> Instance:
+    """The experiment shape of Sec. IV-A / Fig. 5: a fixed total instance size
+    (`total` items over all transactions) at item density `density`, so
+    m = total / (density * n) transactions and |S_i| ~ total / n."""
+    m = max(1, int(round(total / (density * n))))
+    return bernoulli_tidlists(m, n, density, seed + n, s=1, name=f"nsweep{n}")
+
+
 def batch_specs(k: int = 64, seed0: int = 1000, m_range=(1e4, 1e6), n_range=(100, 4000),
                 d_range=(0.01, 0.10)):
     """Instance shapes of the batched workload: m log-uniform, n and density uniform."""

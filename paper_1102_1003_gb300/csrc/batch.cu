@@ -212,7 +212,10 @@ void autotune(batmap_set *const *sets, uint32_t k, double *eff_out, cudaStream_t
         }
         sort_units(&units);
         double padded = 0.0;
-        for (const auto &w : units) padded += (double)SHAPES[w.shape].TR * SHAPES[w.shape].TC * w.klen;
+        for (const auto &w : units) {
+            const ShapeDesc &sh = SHAPES[w.shape & UNIT_SHAPE_MASK];
+            padded += (double)sh.TR * sh.TC * w.klen;
+        }
         DevBuf<WorkUnit> d_units(units.size());
         if (!units.empty())
             BM_CUDA(cudaMemcpyAsync(d_units.p, units.data(), units.size() * sizeof(WorkUnit), cudaMemcpyHostToDevice, st));

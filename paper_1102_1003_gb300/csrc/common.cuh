@@ -123,8 +123,10 @@ struct WorkUnit {
     uint32_t r0, r1, c0, c1;
     uint32_t k0, klen;
     uint32_t inst;   // instance index (batched launches), 0 otherwise
-    uint32_t shape;  // tile shape index (0-based)
+    uint32_t shape;  // tile shape index (0-based) | UNIT_WHOLE_K if [k0, k0+klen) is the whole width
 };
+constexpr uint32_t UNIT_WHOLE_K = 0x100u;  // the unit owns its pairs: plain stores, no atomics
+constexpr uint32_t UNIT_SHAPE_MASK = 0xFFu;
 static_assert(sizeof(WorkUnit) == 32, "WorkUnit layout");
 
 // Per-instance device view used by the compare kernel (batched form indexes

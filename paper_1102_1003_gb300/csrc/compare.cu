@@ -208,7 +208,8 @@ __device__ __forceinline__ void process_unit(uint4 *smem, const InstView &V, con
             if (gj < wu.c1 && gi < gj && v) {
                 const uint32_t oj = __ldg(&V.order[gj]);
                 const uint64_t lo = oi < oj ? oi : oj, hi = oi < oj ? oj : oi;
-                atomicAdd(&V.C[lo * n - lo * (lo + 1) / 2 + (hi - lo - 1)], v);
+                uint32_t *dst = &V.C[lo * n - lo * (lo + 1) / 2 + (hi - lo - 1)];
+                if (wu.shape & UNIT_WHOLE_K) *dst = v; else atomicAdd(dst, v);
             }
         }
     }
@@ -335,7 +336,8 @@ __device__ __forceinline__ void process_unit_direct(uint4 *smem, const InstView 
             if (gj < wu.c1 && gi < gj && v) {
                 const uint32_t oj = __ldg(&V.order[gj]);
                 const uint64_t lo = oi < oj ? oi : oj, hi = oi < oj ? oj : oi;
-                atomicAdd(&V.C[lo * n - lo * (lo + 1) / 2 + (hi - lo - 1)], v);
+                uint32_t *dst = &V.C[lo * n - lo * (lo + 1) / 2 + (hi - lo - 1)];
+                if (wu.shape & UNIT_WHOLE_K) *dst = v; else atomicAdd(dst, v);
             }
         }
     }
@@ -386,7 +388,7 @@ k_compare(const InstView *__restrict__ views, const WorkUnit *__restrict__ units
         if (u >= count) break;
         const WorkUnit wu = units[u];
         const InstView V = views[wu.inst];
-        switch (wu.shape) {
+        switch (wu.shape & UNIT_SHAPE_MASK) {
 #define X(i, a, b, c, d, e) case i: process_unit<a, b, c, d, e>(smem, V, wu); break;
             BM_SHAPE_LIST(X)
 #undef X
@@ -480,13 +482,15 @@ void schedule_units(const batmap_set *S, uint32_t force_shape, const double *sha
         for (const Tile2 &t : p.tiles)
             for (uint64_t k0 = 0; k0 < p.K; k0 += klen)
                 out->push_back({t.r0, t.r1, t.c0, t.c1, (uint32_t)k0,
-                                (uint32_t)std::min<uint64_t>(klen, p.K - k0), 0, p.shape});
+                                (uint32_t)std::min<uint64_t>(klen, p.K - k0), 0,
+                                p.shape | (klen >= p.K ? UNIT_WHOLE_K : 0u)});
     }
     sort_units(out);
 }
 
 double unit_cost(const WorkUnit &u) {
-    return (double)SHAPES[u.shape].TR * SHAPES[u.shape].TC * (double)u.klen / SHAPES[u.shape].eff;
+    const ShapeDesc &sh = SHAPES[u.shape & UNIT_SHAPE_MASK];
+    return (double)sh.TR * sh.TC * (double)u.klen / sh.eff;
 }
 
 void sort_units(std::vector<WorkUnit> *units) {
