@@ -56,6 +56,8 @@ def lib():
             L.oracle_pairs_threshold.argtypes = [ctypes.c_uint32, _u64p, _u32p, ctypes.c_uint32,
                                                  _u32p, ctypes.c_uint64]
             L.oracle_kway_list.restype = None
+            L.oracle_kway_elems.restype = ctypes.c_uint64
+            L.oracle_kway_elems.argtypes = [ctypes.c_uint32, _u32p, _u64p, _u32p, _u32p]
             L.oracle_kway_list.argtypes = [ctypes.c_uint64, _u32p, _u32p, _u64p, _u32p, _u32p, _u64p]
             _lib = L
     return _lib
@@ -173,3 +175,13 @@ def kway_counts(offsets, tids, queries) -> np.ndarray:
     lib().oracle_kway_list(len(queries), _p32(qoff), _p32(ids), _p64(offsets), _p32(tids),
                            _p32(scratch), _p64(out))
     return out
+
+
+def kway_elems(offsets, tids, query) -> np.ndarray:
+    """Sorted elements of S_a1 cap ... cap S_ak for one query (a list of item ids)."""
+    offsets, tids = _csr(offsets, tids)
+    ids = np.ascontiguousarray(query, dtype=np.uint32)
+    sizes = np.diff(offsets)
+    out = np.zeros(int(sizes[ids[0]]) + 1 if ids.size else 1, dtype=np.uint32)  # room for S_a1
+    k = int(lib().oracle_kway_elems(ids.size, _p32(ids), _p64(offsets), _p32(tids), _p32(out)))
+    return out[:k].copy()

@@ -94,7 +94,7 @@ uint64_t oracle_pairs_threshold(uint32_t n, const uint64_t *off, const uint32_t 
 /*
  * |S_a1 intersect ... intersect S_ak| by iterated merging (the conjunctive
  * query of Sec. I reduced to repeated two-list intersection).  `scratch`
- * needs room for the shortest list.
+ * needs room for the first list, S_a1.
  */
 uint64_t oracle_kway_count(uint32_t k, const uint32_t *ids, const uint64_t *off,
                            const uint32_t *tids, uint32_t *scratch)
@@ -121,6 +121,17 @@ uint64_t oracle_kway_count(uint32_t k, const uint32_t *ids, const uint64_t *off,
         len = w;
     }
     return len;
+}
+
+/*
+ * The elements of S_a1 intersect ... intersect S_ak (the answer of a
+ * conjunctive query, Sec. I), ascending, into out (room for the first
+ * list, S_a1); returns their number.
+ */
+uint64_t oracle_kway_elems(uint32_t k, const uint32_t *ids, const uint64_t *off,
+                           const uint32_t *tids, uint32_t *out)
+{
+    return oracle_kway_count(k, ids, off, tids, out);
 }
 
 /* Batched k-way queries: query q uses ids[qoff[q] .. qoff[q+1]). */

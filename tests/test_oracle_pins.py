@@ -165,3 +165,15 @@ def test_generators_are_valid_csr():
     p = datagen.permutations(1000, 3)
     for t in range(3):
         assert np.array_equal(np.sort(p[t]), np.arange(1000))
+
+
+def test_kway_elems_matches_python_sets():
+    rng = np.random.default_rng(13)
+    inst = _random_instance(rng, 2000, 20)
+    for _ in range(100):
+        q = rng.choice(inst.n, int(rng.integers(1, 6)), replace=False).tolist()
+        ref = set(inst.tidlist(q[0]).tolist())
+        for a in q[1:]:
+            ref &= set(inst.tidlist(a).tolist())
+        got = oracle.kway_elems(inst.offsets, inst.tids, q)
+        assert got.tolist() == sorted(ref)
