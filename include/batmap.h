@@ -269,6 +269,21 @@ batmap_status batmap_pool_info(const batmap_pool *pool, uint32_t *n_batmaps, uin
 batmap_status intersect_query(const batmap_pool *pool, const uint32_t *h_qoff, const uint32_t *h_ids,
                               uint32_t n_queries, uint64_t *d_counts, cudaStream_t stream);
 
+/*
+ * Materialised answers of conjunctive queries: the elements of
+ * S_a1 cap ... cap S_ak, ascending.  Queries as in intersect_query.
+ *   d_out_off : device uint64[n_queries + 1]; query q's elements are
+ *               d_out[d_out_off[q] .. d_out_off[q+1]).
+ *   d_out     : device uint32[cap].
+ *   n_total   : host; receives the total number of elements.  If it exceeds
+ *               cap, d_out_off is complete, elements beyond cap are not
+ *               written and BATMAP_ERR_CAPACITY is returned.
+ * Synchronises the stream.
+ */
+batmap_status intersect_query_list(const batmap_pool *pool, const uint32_t *h_qoff, const uint32_t *h_ids,
+                                   uint32_t n_queries, uint64_t *d_out_off, uint32_t *d_out, uint64_t cap,
+                                   uint64_t *n_total, cudaStream_t stream);
+
 /* Options of the serving loop. */
 typedef struct batmap_serve_opts {
     uint32_t max_batch;   /* queries per micro-batch (default 64)                        */

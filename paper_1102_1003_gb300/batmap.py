@@ -28,7 +28,7 @@ EXPORTED = [
     "batmap_get_info", "batmap_export_layout", "pair_support_all", "pair_support_host",
     "pair_support_batch", "batmap_get_timing", "batmap_kernel_launches", "pair_threshold_noalloc",
     "pair_support_dense", "batmap_pool_create", "batmap_pool_free", "batmap_pool_info", "intersect_query",
-    "batmap_serve", "batmap_autotune", "batmap_release_scratch",
+    "batmap_serve", "batmap_autotune", "batmap_release_scratch", "intersect_query_list",
 ]
 
 
@@ -134,6 +134,8 @@ def load_library(path: str = LIB_PATH):
     L.batmap_pool_info.restype = ctypes.c_int
     L.intersect_query.argtypes = [vp, vp, vp, u32, vp, vp]
     L.intersect_query.restype = ctypes.c_int
+    L.intersect_query_list.argtypes = [vp, vp, vp, u32, vp, vp, u64, ctypes.POINTER(u64), vp]
+    L.intersect_query_list.restype = ctypes.c_int
     L.batmap_serve.argtypes = [vp, vp, vp, vp, u32, ctypes.POINTER(batmap_serve_opts), vp, vp,
                                ctypes.POINTER(batmap_serve_stats), vp]
     L.batmap_serve.restype = ctypes.c_int
@@ -399,6 +401,25 @@ def intersect_query(pool: BatMapPool, queries, counts=None, stream=None):
     _check(load_library().intersect_query(pool.handle, qoff.ctypes.data, ids.ctypes.data, len(queries),
                                           _ptr(counts), _stream_handle(stream)))
     return counts[:len(queries)]
+
+
+def intersect_query_list(pool: BatMapPool, queries, stream=None):
+    """Elements of each query's intersection; returns (offsets int64 [nq+1], elements int32),
+    both cuda tensors.  Sizes the output with a first counting call."""
+    import torch
+    L = load_library()
+    qoff, ids = _queries_csr(queries)
+    nq = len(queries)
+    off = torch.zeros(nq + 1, dtype=torch.int64, device="cuda")
+    total = ctypes.c_uint64(0)
+    st = _stream_handle(stream)
+    rc = L.intersect_query_list(pool.handle, qoff.ctypes.data, ids.ctypes.data, nq, _ptr(off), None, 0,
+                                ctypes.byref(total), st)
+    _check(rc, allow=(BATMAP_ERR_CAPACITY,))
+    out = torch.empty(max(int(total.value), 1), dtype=torch.int32, device="cuda")
+    _check(L.intersect_query_list(pool.handle, qoff.ctypes.data, ids.ctypes.data, nq, _ptr(off), _ptr(out),
+                                  out.numel(), ctypes.byref(total), st))
+    return off, out[:int(total.value)]
 
 
 def batmap_serve(pool: BatMapPool, queries, arrival_s, opts: batmap_serve_opts | None = None, stream=None):

@@ -21,6 +21,7 @@
 #include <thread>
 
 #include "common.cuh"
+#include "scan.cuh"
 
 namespace bm {
 
@@ -96,6 +97,63 @@ __global__ void k_probe(PoolView P, const QueryDesc *__restrict__ qs, const Prob
         for (int d = 16; d > 0; d >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, d);
         if (lane == 0 && cnt) atomicAdd(&counts[tk.q], (unsigned long long)cnt);
     }
+}
+
+// Materialised answers: the count pass stores one count per task; after an
+// exclusive scan over tasks the write pass lists each task's matches in
+// element order (a warp ballot ranks them), so every answer is ascending.
+__global__ void k_probe_count(PoolView P, const QueryDesc *__restrict__ qs, const ProbeTask *__restrict__ tasks,
+                              uint32_t ntasks, uint64_t *__restrict__ task_counts) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < ntasks; w += warps) {
+        const ProbeTask tk = tasks[w];
+        const QueryDesc &Q = qs[tk.q];
+        const uint64_t a0 = P.off[Q.ids[0]];
+        uint32_t cnt = 0;
+        for (uint32_t i = tk.begin + lane; i < tk.end; i += 32) {
+            const uint32_t x = P.tids[a0 + i];
+            bool in_all = true;
+            for (uint32_t t = 1; t < Q.k && in_all; t++) in_all = member(P, Q.ids[t], x);
+            cnt += in_all ? 1u : 0u;
+        }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, d);
+        if (lane == 0) task_counts[w] = cnt;
+    }
+}
+
+__global__ void k_probe_write(PoolView P, const QueryDesc *__restrict__ qs, const ProbeTask *__restrict__ tasks,
+                              uint32_t ntasks, const uint64_t *__restrict__ task_off, uint32_t *__restrict__ out,
+                              uint64_t cap) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < ntasks; w += warps) {
+        const ProbeTask tk = tasks[w];
+        const QueryDesc &Q = qs[tk.q];
+        const uint64_t a0 = P.off[Q.ids[0]];
+        uint64_t running = task_off[w];
+        for (uint32_t base = tk.begin; base < tk.end; base += 32) {
+            const uint32_t i = base + lane;
+            bool in_all = false;
+            uint32_t x = 0;
+            if (i < tk.end) {
+                x = P.tids[a0 + i];
+                in_all = true;
+                for (uint32_t t = 1; t < Q.k && in_all; t++) in_all = member(P, Q.ids[t], x);
+            }
+            const uint32_t mask = __ballot_sync(0xffffffffu, in_all);
+            const uint64_t pos = running + __popc(mask & ((1u << lane) - 1u));
+            if (in_all && pos < cap) out[pos] = x;
+            running += __popc(mask);
+        }
+    }
+}
+
+__global__ void k_query_offsets(const uint64_t *__restrict__ task_off, const uint32_t *__restrict__ first_task,
+                                uint32_t nq, uint64_t *__restrict__ out_off) {
+    const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q <= nq) out_off[q] = task_off[first_task[q]];
 }
 
 // One warp per set: every tid < m and strictly increasing within its set.
@@ -311,6 +369,46 @@ static uint64_t query_work(const batmap_pool *pool, const uint32_t *qoff, const 
         if (c < pool->n) small = std::min<uint64_t>(small, pool->h_off[c + 1] - pool->h_off[c]);
     }
     return (small == UINT64_MAX ? 0 : small) * (qoff[q + 1] - qoff[q]) + 1;
+}
+
+// Answers as element lists: out_off[q] .. out_off[q+1] in out (ascending).
+static void intersect_list(const batmap_pool *pool, const uint32_t *qoff, const uint32_t *ids, uint32_t nq,
+                           uint64_t *d_out_off, uint32_t *d_out, uint64_t cap, uint64_t *n_total, cudaStream_t st) {
+    BM_REQUIRE(pool && qoff && n_total && d_out_off, BATMAP_ERR_ARG, "NULL argument");
+    BM_REQUIRE(cap == 0 || d_out, BATMAP_ERR_ARG, "d_out is NULL with cap > 0");
+    std::vector<QueryDesc> qs;
+    std::vector<ProbeTask> tasks;
+    if (nq) prepare_batch(pool, qoff, ids, 0, nq, &qs, &tasks);
+    const uint64_t nt = tasks.size();
+    std::vector<uint32_t> first(nq + 1, (uint32_t)nt);
+    for (uint64_t t = nt; t-- > 0;) first[tasks[t].q] = (uint32_t)t;
+    for (uint32_t q = nq; q-- > 0;) first[q] = std::min(first[q], first[q + 1]);
+    DevBuf<QueryDesc> d_q(std::max<uint64_t>(qs.size(), 1));
+    DevBuf<ProbeTask> d_t(std::max<uint64_t>(nt, 1));
+    DevBuf<uint64_t> d_toff(nt + 1), d_total(1);
+    DevBuf<uint32_t> d_first(nq + 1);
+    if (nq) BM_CUDA(cudaMemcpyAsync(d_q.p, qs.data(), qs.size() * sizeof(QueryDesc), cudaMemcpyHostToDevice, st));
+    if (nt) BM_CUDA(cudaMemcpyAsync(d_t.p, tasks.data(), nt * sizeof(ProbeTask), cudaMemcpyHostToDevice, st));
+    BM_CUDA(cudaMemcpyAsync(d_first.p, first.data(), (nq + 1) * 4ull, cudaMemcpyHostToDevice, st));
+    const unsigned blocks = (unsigned)std::min<uint64_t>((nt + 7) / 8, 4096);
+    if (nt) {
+        k_probe_count<<<blocks, 256, 0, st>>>(pool->view, d_q.p, d_t.p, (uint32_t)nt, d_toff.p);
+        BM_CHECK_LAUNCH();
+    }
+    k_scan_single_block<<<1, SCAN_TPB, 0, st>>>(d_toff.p, nt, d_total.p, 1);
+    BM_CHECK_LAUNCH();
+    k_query_offsets<<<(nq + 1 + 255) / 256, 256, 0, st>>>(d_toff.p, d_first.p, nq, d_out_off);
+    BM_CHECK_LAUNCH();
+    if (nt && cap) {
+        k_probe_write<<<blocks, 256, 0, st>>>(pool->view, d_q.p, d_t.p, (uint32_t)nt, d_toff.p, d_out, cap);
+        BM_CHECK_LAUNCH();
+    }
+    uint64_t total = 0;
+    BM_CUDA(cudaMemcpyAsync(&total, d_total.p, 8, cudaMemcpyDeviceToHost, st));
+    BM_CUDA(cudaStreamSynchronize(st));
+    *n_total = total;
+    if (total > cap)
+        throw Error{BATMAP_ERR_CAPACITY, "d_out too small: " + std::to_string(total) + " elements in the answers"};
 }
 
 // Staging for one in-flight batch (pinned host + device, fixed capacity).
@@ -546,6 +644,12 @@ batmap_status intersect_query(const batmap_pool *pool, const uint32_t *h_qoff, c
                               uint32_t n_queries, uint64_t *d_counts, cudaStream_t stream) {
     BM_GUARD(bm::intersect(pool, h_qoff, h_ids, n_queries, reinterpret_cast<unsigned long long *>(d_counts),
                            stream));
+}
+
+batmap_status intersect_query_list(const batmap_pool *pool, const uint32_t *h_qoff, const uint32_t *h_ids,
+                                   uint32_t n_queries, uint64_t *d_out_off, uint32_t *d_out, uint64_t cap,
+                                   uint64_t *n_total, cudaStream_t stream) {
+    BM_GUARD(bm::intersect_list(pool, h_qoff, h_ids, n_queries, d_out_off, d_out, cap, n_total, stream));
 }
 
 batmap_status batmap_serve(const batmap_pool *pool, const uint32_t *h_qoff, const uint32_t *h_ids,

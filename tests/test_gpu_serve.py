@@ -89,3 +89,20 @@ def test_pool_rejects_bad_input():
     with pytest.raises(pkg.BatmapError) as e:
         _make_pool(inst)
     assert e.value.code == pkg.BATMAP_ERR_ARG
+
+
+@pytest.mark.parametrize("params", [None, dict(load_num=1, load_den=2, max_loop=1)])
+def test_intersect_query_list_exact(params):
+    import paper_1102_1003_gb300 as pkg
+    inst = _pool_inst()
+    pool = _make_pool(inst, params=pkg.batmap_default_params(**params) if params else None)
+    qs = _queries(inst.n, 400, 19, np.flatnonzero(inst.sizes >= 8192))
+    off, elems = pkg.intersect_query_list(pool, qs)
+    off = off.cpu().numpy()
+    elems = elems.cpu().numpy().astype(np.uint32)
+    assert off[0] == 0 and off[-1] == elems.size and (np.diff(off) >= 0).all()
+    counts = pkg.intersect_query(pool, qs).cpu().numpy()
+    for q, query in enumerate(qs):
+        ref = oracle.kway_elems(inst.offsets, inst.tids, query)
+        assert np.array_equal(elems[off[q]:off[q + 1]], ref), q
+        assert counts[q] == ref.size
