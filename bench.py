@@ -479,6 +479,101 @@ def run_nsweep(args):
                       "rows": rows}), flush=True)
 
 
+def run_cross(args):
+    """Sparse boolean matrix multiplication / join-project (Sec. I): the supports
+    |A_i cap B_j| of every pair across two families and the pairs with a
+    nonempty intersection (s = 1).  One step = cross build + compare + list."""
+    import torch
+    import paper_1102_1003_gb300 as pkg
+    import oracle
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    L = pkg.load_library()
+    union, na = datagen.cross_instance()
+    nb = union.n - na
+    npairs = na * nb
+    off = torch.from_numpy(union.offsets.view(np.int64)).to(dev)
+    tids = torch.from_numpy(union.tids.view(np.int32)).to(dev)
+    perm = torch.from_numpy(datagen.permutations(union.m, 5).view(np.int32)).to(dev)
+    full = torch.empty(npairs, dtype=torch.int32, device=dev)
+    b = pkg.batmap_build_cross(union.m, na, off, tids, perm)
+    n_out, _ = pkg.pair_support_all(b, 1)
+    info = b.info
+    b.free()
+    pairs = torch.empty((max(n_out, 1), 3), dtype=torch.int32, device=dev)
+
+    def step():
+        bs = pkg.batmap_build_cross(union.m, na, off, tids, perm)
+        k, _ = pkg.pair_support_all(bs, 1, pairs=pairs, full=full)
+        t = pkg.batmap_get_timing(bs)
+        bs.free()
+        return k, t
+
+    for _ in range(args.warmup):
+        step()
+    stream = torch.cuda.current_stream()
+    sampler = ClockSampler(0)
+    sampler.start()
+    torch.cuda.synchronize()
+    launches0 = L.batmap_kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    phases = []
+    for _ in range(args.steps):
+        k, t = step()
+        phases.append(t)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    launches = L.batmap_kernel_launches() - launches0
+    clocks = sampler.stop()
+    assert k == n_out
+    # sampled parity against the oracle on the union (B's items follow A's)
+    rng = np.random.default_rng(5)
+    ia = rng.integers(0, na, 4000)
+    jb = rng.integers(0, nb, 4000)
+    ref = oracle.pairs_list(union.offsets, union.tids, ia, na + jb, threads=os.cpu_count() or 4)
+    got = full.cpu().numpy().astype(np.uint32)[ia * nb + jb]
+    peaks, peak_kind = _peaks()
+    cmp_s = statistics.mean(t["compare_ms"] for t in phases) / 1e3
+    wp = info["word_pairs"]
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_peak = sms * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    achieved = OPS_PER_WORD_PAIR * wp / cmp_s / 1e12
+    line = {"metric": "A x B pair supports/sec (sparse boolean matrix multiplication), bit-exact",
+            "workload": "cross", "unit": UNIT, "value": npairs * args.steps / elapsed, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": "cross", "m": union.m, "n_a": na, "n_b": nb, "s": 1, "pairs": npairs,
+                       "desc": "A: Zipf(1) sizes at mean density 1%; B: Bernoulli p=0.002",
+                       "tids": int(union.tids.size), "batmap_bytes": int(info["bytes"]),
+                       "l2": "inputs larger than L2 (no flush)"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
+                         "frac": achieved / alu_peak, "kernel": "k_compare", "traffic": None,
+                         "peak_kind": f"{sms} SMs x 128 INT32 lanes x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz "
+                                      f"({peak_kind} max clock)",
+                         "algorithmic_ops": f"{OPS_PER_WORD_PAIR} x {wp:.4g} word pairs"},
+            "phases_ms": {p: statistics.mean(t[p] for t in phases) for p in ("build_ms", "compare_ms", "compact_ms")},
+            "nonempty_pairs": n_out, "failed_insertions": info["n_failed"], "gpu_launches": int(launches),
+            "parity_sample": {"pairs": int(ia.size), "exact": bool(np.array_equal(got, ref))},
+            "clocks": clocks}
+    if not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        kk = 20000
+        t0 = time.perf_counter()
+        oracle.pairs_list(union.offsets, union.tids, rng.integers(0, na, kk), na + rng.integers(0, nb, kk),
+                          threads=cores)
+        dt = time.perf_counter() - t0
+        kk = int(min(max(kk * args.cpu_seconds / max(dt, 1e-6), kk), npairs))
+        ia, jb = rng.integers(0, na, kk), rng.integers(0, nb, kk)
+        t0 = time.perf_counter()
+        oracle.pairs_list(union.offsets, union.tids, ia, na + jb, threads=cores)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": kk / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"{kk} uniformly sampled A x B pairs, {dt:.1f} s"}
+    print(json.dumps(line), flush=True)
+
+
 def run_serve(args):
     """Serving workload: pool of sets over 2^26 with Zipf sizes on [10, 1e6],
     Poisson-arriving queries (80% pairs, 20% 3..8-way), continuous batching."""
@@ -563,7 +658,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["mine", "reference"], default="mine")
-    ap.add_argument("--workload", choices=sorted(WORKLOAD_DESC) + ["serve", "batch", "nsweep"], default="cfg2")
+    ap.add_argument("--workload", choices=sorted(WORKLOAD_DESC) + ["serve", "batch", "nsweep", "cross"], default="cfg2")
     ap.add_argument("--nsweep", type=int, nargs="+", default=[1000, 2000, 4000, 8000, 16000, 32000, 64000])
     ap.add_argument("--instances", type=int, default=64, help="instances (batch workload)")
     ap.add_argument("--no-autotune", action="store_true")
@@ -577,9 +672,9 @@ def main():
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
-    if args.workload in ("serve", "batch", "nsweep"):
+    if args.workload in ("serve", "batch", "nsweep", "cross"):
         if rank == 0:
-            {"serve": run_serve, "batch": run_batch, "nsweep": run_nsweep}[args.workload](args)
+            {"serve": run_serve, "batch": run_batch, "nsweep": run_nsweep, "cross": run_cross}[args.workload](args)
         return
     inst = datagen.config_instance(args.workload)
     if args.impl == "reference":

@@ -32,7 +32,7 @@ __all__ = [
     "Instance", "bernoulli_item", "bernoulli_tidlists", "zipf_probabilities",
     "zipf_tidlists", "permutations", "config_instance", "batch_specs",
     "pool_sizes", "pool_tidlists", "from_lists", "transactions_to_tidlists",
-    "CONFIGS",
+    "CONFIGS", "concat", "cross_instance",
 ]
 
 
@@ -168,6 +168,28 @@ def nsweep_instance(n: int, total: int = 10_000_000, density: float = 0.05, seed
     m = total / (density * n) transactions and |S_i| ~ total / n."""
     m = max(1, int(round(total / (density * n))))
     return bernoulli_tidlists(m, n, density, seed + n, s=1, name=f"nsweep{n}")
+
+
+def concat(a: Instance, b: Instance, name: str = "") -> Instance:
+    """Family A's tidlists followed by family B's, over the same m (cross mode input)."""
+    assert a.m == b.m
+    offsets = np.concatenate([a.offsets, a.offsets[-1] + b.offsets[1:]]).astype(np.uint64)
+    return Instance(m=a.m, n=a.n + b.n, offsets=offsets, tids=np.concatenate([a.tids, b.tids]),
+                    s=1, name=name)
+
+
+CROSS = dict(m=1_000_000, n_a=2_000, density_a=0.01, n_b=4_000, p_b=0.002, seed=61)
+
+
+def cross_instance(m: int = CROSS["m"], n_a: int = CROSS["n_a"], n_b: int = CROSS["n_b"],
+                   density_a: float = CROSS["density_a"], p_b: float = CROSS["p_b"],
+                   seed: int = CROSS["seed"]) -> tuple[Instance, int]:
+    """Sparse boolean matrix multiplication / join-project shape (Sec. I): rows
+    A_i of one matrix (Zipf(1) sizes at mean density `density_a`) against
+    columns B_j of another (Bernoulli `p_b`); returns (A then B, n_a)."""
+    a = zipf_tidlists(m, n_a, density_a, seed)
+    b = bernoulli_tidlists(m, n_b, p_b, seed + 1)
+    return concat(a, b, name="cross"), n_a
 
 
 def batch_specs(k: int = 64, seed0: int = 1000, m_range=(1e4, 1e6), n_range=(100, 4000),

@@ -90,8 +90,8 @@ typedef struct batmap_info {
     uint64_t n_corrections;  /* correction entries (one per failed common tid) */
     uint64_t n_work_units;   /* compare work units scheduled                   */
     uint32_t n_classes;      /* distinct BatMap widths                         */
-    uint32_t reserved;
-    double word_pairs;       /* sum over pairs i<j of max(|B_i|,|B_j|)/4       */
+    uint32_t n_a;            /* cross mode: size of family A (0 = all pairs)    */
+    double word_pairs;       /* sum over reported pairs of max(|B_i|,|B_j|)/4  */
 } batmap_info;
 
 /* Fills *p with the defaults documented above. */
@@ -126,6 +126,20 @@ const char *batmap_last_error(void);
 batmap_status batmap_build(const batmap_params *p, uint32_t m, uint32_t n,
                            const uint64_t *d_offsets, const uint32_t *d_tids,
                            const uint32_t *d_perm, cudaStream_t stream, batmap_set **out);
+
+/*
+ * Cross mode: the supports |A_i cap B_j| between two families of sets over
+ * the same transactions (Sec. I: sparse boolean matrix multiplication and
+ * join-project reduce to these intersections; pairs with support >= 1 are
+ * the non-zeros of the boolean product).  The CSR holds n_a sets of family A
+ * followed by n_b sets of family B; otherwise as batmap_build.  On a set
+ * built this way, pair_support_all reports the n_a x n_b supports: d_full is
+ * uint32[n_a * n_b] row-major (A item, B item), and the triples are
+ * (a, b, support) with a in [0, n_a) and b in [0, n_b), lexicographic.
+ */
+batmap_status batmap_build_cross(const batmap_params *p, uint32_t m, uint32_t n_a, uint32_t n_b,
+                                 const uint64_t *d_offsets, const uint32_t *d_tids, const uint32_t *d_perm,
+                                 cudaStream_t stream, batmap_set **out);
 
 /* Release a handle and all device memory it owns (NULL is ignored). */
 void batmap_free(batmap_set *set);

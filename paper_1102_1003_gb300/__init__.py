@@ -12,5 +12,5 @@ from .batmap import (  # noqa: F401
     load_library, pair_support_all,
     pair_support_batch, pair_support_dense, pair_support_host, pair_threshold_noalloc,
     BatMapPool, batmap_pool_create, batmap_pool_free, batmap_pool_info, intersect_query, batmap_serve,
-    batmap_serve_opts, batmap_autotune, batmap_release_scratch, intersect_query_list,
+    batmap_serve_opts, batmap_autotune, batmap_release_scratch, intersect_query_list, batmap_build_cross,
 )

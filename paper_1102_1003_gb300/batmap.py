@@ -28,7 +28,7 @@ EXPORTED = [
     "batmap_get_info", "batmap_export_layout", "pair_support_all", "pair_support_host",
     "pair_support_batch", "batmap_get_timing", "batmap_kernel_launches", "pair_threshold_noalloc",
     "pair_support_dense", "batmap_pool_create", "batmap_pool_free", "batmap_pool_info", "intersect_query",
-    "batmap_serve", "batmap_autotune", "batmap_release_scratch", "intersect_query_list",
+    "batmap_serve", "batmap_autotune", "batmap_release_scratch", "intersect_query_list", "batmap_build_cross",
 ]
 
 
@@ -44,11 +44,11 @@ class batmap_info(ctypes.Structure):
                 ("r0", ctypes.c_uint32), ("bytes", ctypes.c_uint64),
                 ("n_elements", ctypes.c_uint64), ("n_failed", ctypes.c_uint64),
                 ("n_corrections", ctypes.c_uint64), ("n_work_units", ctypes.c_uint64),
-                ("n_classes", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("n_classes", ctypes.c_uint32), ("n_a", ctypes.c_uint32),
                 ("word_pairs", ctypes.c_double)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class batmap_timing(ctypes.Structure):
@@ -105,6 +105,9 @@ def load_library(path: str = LIB_PATH):
     L.batmap_build.argtypes = [ctypes.POINTER(batmap_params), u32, u32, vp, vp, vp, vp,
                                ctypes.POINTER(vp)]
     L.batmap_build.restype = ctypes.c_int
+    L.batmap_build_cross.argtypes = [ctypes.POINTER(batmap_params), u32, u32, u32, vp, vp, vp, vp,
+                                      ctypes.POINTER(vp)]
+    L.batmap_build_cross.restype = ctypes.c_int
     L.batmap_free.argtypes = [vp]
     L.batmap_free.restype = None
     L.batmap_get_info.argtypes = [vp, ctypes.POINTER(batmap_info)]
@@ -207,6 +210,22 @@ def batmap_build(m: int, offsets, tids, perm, params: batmap_params | None = Non
     _check(L.batmap_build(pp, int(m), n, _ptr(offsets), _ptr(tids) if tids.numel() else None,
                           _ptr(perm), _stream_handle(stream), ctypes.byref(h)))
     return BatMapSet(h, int(m), n)
+
+
+def batmap_build_cross(m: int, n_a: int, offsets, tids, perm, params: batmap_params | None = None,
+                       stream=None) -> BatMapSet:
+    """Cross-mode set: the CSR holds n_a sets of family A then the sets of family B;
+    pair_support_all then reports the n_a x n_b supports |A_i cap B_j|."""
+    L = load_library()
+    n = int(offsets.numel()) - 1
+    h = ctypes.c_void_p()
+    pp = ctypes.byref(params) if params is not None else None
+    _check(L.batmap_build_cross(pp, int(m), int(n_a), n - int(n_a), _ptr(offsets),
+                                _ptr(tids) if tids.numel() else None, _ptr(perm), _stream_handle(stream),
+                                ctypes.byref(h)))
+    b = BatMapSet(h, int(m), n)
+    b.n_a = int(n_a)
+    return b
 
 
 def batmap_free(bset: BatMapSet):

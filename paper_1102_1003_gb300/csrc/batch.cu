@@ -57,8 +57,8 @@ static std::vector<uint64_t> plan_key(batmap_set *const *sets, const uint32_t *s
 static void enqueue_batch(BatchPlan *P, batmap_set *const *sets, const uint32_t *s, uint32_t k,
                           const batmap_out *outs, cudaStream_t st) {
     for (uint32_t q = 0; q < k; q++) {
-        const uint64_t n = sets[q]->n;
-        if (n > 1) BM_CUDA(cudaMemsetAsync(P->C[q], 0, n * (n - 1) / 2 * sizeof(uint32_t), st));
+        const uint64_t np = sets[q]->npairs();
+        if (np) BM_CUDA(cudaMemsetAsync(P->C[q], 0, np * sizeof(uint32_t), st));
     }
     BM_CUDA(cudaMemsetAsync(P->d_counter.p, 0, sizeof(uint32_t), st));
     launch_compare(P->d_views.p, P->d_units.p, P->nunits, P->d_counter.p,
@@ -80,12 +80,12 @@ static BatchPlan *make_plan(batmap_set *const *sets, const uint32_t *s, uint32_t
         const uint64_t n = S->n;
         uint32_t *C = outs[q].d_full;
         if (!C) {
-            S->d_C.ensure(n * (n - 1) / 2);
+            S->d_C.ensure(S->npairs());
             C = S->d_C.p;
         }
         P->C[q] = C;
         views[q] = InstView{reinterpret_cast<const uint4 *>(S->d_bm.p), S->d_line_off.p, S->d_wshift.p,
-                            S->d_order.p, C, S->n, 0};
+                            S->d_order.p, C, S->n, S->n_a};
         for (WorkUnit u : S->units) {
             u.inst = q;
             units.push_back(u);
@@ -182,7 +182,7 @@ void autotune(batmap_set *const *sets, uint32_t k, double *eff_out, cudaStream_t
     std::vector<uint32_t> idx;
     for (uint32_t q = 0; q < k; q++) {
         BM_REQUIRE(sets[q], BATMAP_ERR_ARG, "NULL set");
-        if (sets[q]->n > 1) idx.push_back(q);
+        if (sets[q]->npairs()) idx.push_back(q);
     }
     BM_REQUIRE(!idx.empty(), BATMAP_ERR_ARG, "no set with a pair to tune on");
     std::sort(idx.begin(), idx.end(), [&](uint32_t a, uint32_t b) { return sets[a]->word_pairs > sets[b]->word_pairs; });
@@ -191,9 +191,9 @@ void autotune(batmap_set *const *sets, uint32_t k, double *eff_out, cudaStream_t
     for (uint32_t q : idx) {
         batmap_set *S = sets[q];
         const uint64_t n = S->n;
-        S->d_C.ensure(n * (n - 1) / 2);
+        S->d_C.ensure(S->npairs());
         views.push_back(InstView{reinterpret_cast<const uint4 *>(S->d_bm.p), S->d_line_off.p, S->d_wshift.p,
-                                 S->d_order.p, S->d_C.p, S->n, 0});
+                                 S->d_order.p, S->d_C.p, S->n, S->n_a});
     }
     DevBuf<InstView> d_views(views.size());
     DevBuf<uint32_t> d_counter(1);

@@ -365,8 +365,12 @@ void build_set(batmap_set *S, const uint64_t *d_offsets, const uint32_t *d_tids,
     }
     S->order.resize(n);
     std::iota(S->order.begin(), S->order.end(), 0u);
-    std::stable_sort(S->order.begin(), S->order.end(),
-                     [&](uint32_t a, uint32_t b) { return rlog[a] < rlog[b]; });
+    // width-sorted (stable by id); in cross mode family A [0, n_a) first
+    const uint32_t na = S->n_a;
+    std::stable_sort(S->order.begin(), S->order.end(), [&](uint32_t a, uint32_t b) {
+        const bool fa = na && a >= na, fb = na && b >= na;
+        return fa != fb ? fb : rlog[a] < rlog[b];
+    });
     S->rank.assign(n, 0);
     S->byte_off.assign(n, 0);
     S->wshift_sorted.assign(n, 0);
@@ -382,7 +386,7 @@ void build_set(batmap_set *S, const uint64_t *d_offsets, const uint32_t *d_tids,
         BM_REQUIRE(pos / 128 < (1ull << 32), BATMAP_ERR_ARG, "BatMap array exceeds 512 GB");
         line_off[q] = (uint32_t)(pos / 128);
         S->wshift_sorted[q] = rlog[i] - 2;
-        if (q == 0 || rlog[S->order[q - 1]] != rlog[i]) S->class_begin.push_back(q);
+        if (q == 0 || rlog[S->order[q - 1]] != rlog[i] || (na && q == na)) S->class_begin.push_back(q);
         pos += 3ull << rlog[i];
     }
     S->class_begin.push_back(n);
@@ -392,7 +396,19 @@ void build_set(batmap_set *S, const uint64_t *d_offsets, const uint32_t *d_tids,
 
     // algorithmic work of the compare: sum over pairs of the wider width / 4
     double wp = 0.0;
-    for (uint32_t q = 0; q < n; q++) wp += (double)q * (double)((3ull << (S->wshift_sorted[q] + 2)) / 4);
+    if (!na) {
+        for (uint32_t q = 0; q < n; q++) wp += (double)q * (double)((3ull << (S->wshift_sorted[q] + 2)) / 4);
+    } else {
+        // both families are width-sorted: A items no wider than b contribute b's width,
+        // the wider ones their own (suffix sums over A)
+        std::vector<double> suffix(na + 1, 0.0);
+        for (uint32_t a = na; a-- > 0;) suffix[a] = suffix[a + 1] + (double)(3ull << S->wshift_sorted[a]);
+        uint32_t a = 0;
+        for (uint32_t b = na; b < n; b++) {
+            while (a < na && S->wshift_sorted[a] <= S->wshift_sorted[b]) a++;
+            wp += (double)a * (double)(3ull << S->wshift_sorted[b]) + suffix[a];
+        }
+    }
     S->word_pairs = wp;
 
     // ---- device metadata ----

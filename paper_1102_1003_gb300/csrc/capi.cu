@@ -47,7 +47,7 @@ static batmap_status guarded(F &&f) {
 // Zero C, run every shape's persistent compare launch over the set's units.
 void enqueue_compare(batmap_set *S, uint32_t *C, const InstView *d_view, cudaStream_t st) {
     const uint64_t n = S->n;
-    const uint64_t npairs = n * (n - 1) / 2;
+    const uint64_t npairs = S->npairs();
     if (npairs) BM_CUDA(cudaMemsetAsync(C, 0, npairs * sizeof(uint32_t), st));
     S->d_counters.ensure(1);
     BM_CUDA(cudaMemsetAsync(S->d_counters.p, 0, sizeof(uint32_t), st));
@@ -77,9 +77,9 @@ void batmap_default_params(batmap_params *p) {
 
 const char *batmap_last_error(void) { return g_last_error.c_str(); }
 
-batmap_status batmap_build(const batmap_params *p, uint32_t m, uint32_t n, const uint64_t *d_offsets,
-                           const uint32_t *d_tids, const uint32_t *d_perm, cudaStream_t stream,
-                           batmap_set **out) {
+static batmap_status build_any(const batmap_params *p, uint32_t m, uint32_t n, uint32_t n_a,
+                               const uint64_t *d_offsets, const uint32_t *d_tids, const uint32_t *d_perm,
+                               cudaStream_t stream, batmap_set **out) {
     return guarded([&] {
         BM_REQUIRE(out != nullptr, BATMAP_ERR_ARG, "out is NULL");
         *out = nullptr;
@@ -97,6 +97,7 @@ batmap_status batmap_build(const batmap_params *p, uint32_t m, uint32_t n, const
         S->m = m;
         S->n = n;
         S->stream = stream;
+        S->n_a = n_a;
         S->gen = g_gen.fetch_add(1);
         try {
             build_set(S, d_offsets, d_tids, d_perm);
@@ -106,6 +107,26 @@ batmap_status batmap_build(const batmap_params *p, uint32_t m, uint32_t n, const
         }
         *out = S;
     });
+}
+
+batmap_status batmap_build(const batmap_params *p, uint32_t m, uint32_t n, const uint64_t *d_offsets,
+                           const uint32_t *d_tids, const uint32_t *d_perm, cudaStream_t stream,
+                           batmap_set **out) {
+    return build_any(p, m, n, 0, d_offsets, d_tids, d_perm, stream, out);
+}
+
+batmap_status batmap_build_cross(const batmap_params *p, uint32_t m, uint32_t n_a, uint32_t n_b,
+                                 const uint64_t *d_offsets, const uint32_t *d_tids, const uint32_t *d_perm,
+                                 cudaStream_t stream, batmap_set **out) {
+    if (n_a == 0 || n_b == 0) {
+        set_error("batmap_build_cross needs two non-empty families");
+        return BATMAP_ERR_ARG;
+    }
+    if ((uint64_t)n_a + n_b > 0xFFFFFFFFull) {
+        set_error("n_a + n_b exceeds 2^32 - 1");
+        return BATMAP_ERR_ARG;
+    }
+    return build_any(p, m, n_a + n_b, n_a, d_offsets, d_tids, d_perm, stream, out);
 }
 
 void batmap_free(batmap_set *set) {
@@ -129,6 +150,7 @@ batmap_status batmap_get_info(const batmap_set *S, batmap_info *info) {
         info->n_corrections = S->n_corr;
         info->n_work_units = S->units.size();
         info->n_classes = S->class_begin.empty() ? 0 : (uint32_t)S->class_begin.size() - 1;
+        info->n_a = S->n_a;
         info->word_pairs = S->word_pairs;
     });
 }
@@ -160,7 +182,7 @@ static void pair_support_impl(batmap_set *S, uint32_t s, uint32_t *d_pairs, uint
     BM_REQUIRE(n_out, BATMAP_ERR_ARG, "n_out is NULL");
     BM_REQUIRE(cap == 0 || d_pairs, BATMAP_ERR_ARG, "d_pairs is NULL with cap > 0");
     const uint64_t n = S->n;
-    const uint64_t npairs = n * (n - 1) / 2;
+    const uint64_t npairs = S->npairs();
     uint32_t *C = d_full;
     if (!C) {
         S->d_C.ensure(npairs);
@@ -168,7 +190,7 @@ static void pair_support_impl(batmap_set *S, uint32_t s, uint32_t *d_pairs, uint
     }
     static thread_local InstView h_view;
     h_view = InstView{reinterpret_cast<const uint4 *>(S->d_bm.p), S->d_line_off.p, S->d_wshift.p,
-                      S->d_order.p, C, S->n, 0};
+                      S->d_order.p, C, S->n, S->n_a};
     S->d_total.ensure(1);
     S->d_view.ensure(1);
     S->pairs_ev.create();

@@ -136,10 +136,17 @@ struct InstView {
     const uint32_t *line_off; // [n] sorted order: byte offset / 128 of each BatMap
     const uint32_t *wshift;   // [n] sorted order: e with |B|/4 words = 3 * 2^e
     const uint32_t *order;    // [n] sorted position -> original item id
-    uint32_t *C;              // packed upper triangle of supports (original ids)
+    uint32_t *C;              // supports: packed upper triangle (original ids), or n_a x (n - n_a) in cross mode
     uint32_t n;
-    uint32_t pad;
+    uint32_t n_a;             // 0: all pairs i < j; else cross pairs of items [0, n_a) with [n_a, n)
 };
+
+// Index of the support of the pair of original items (oi, oj) in C.
+__device__ __forceinline__ uint64_t support_index(uint32_t oi, uint32_t oj, uint64_t n, uint32_t n_a) {
+    const uint64_t lo = oi < oj ? oi : oj, hi = oi < oj ? oj : oi;
+    if (n_a) return lo * (n - n_a) + (hi - n_a);
+    return lo * n - lo * (lo + 1) / 2 + (hi - lo - 1);
+}
 
 }  // namespace bm
 
@@ -147,8 +154,12 @@ struct InstView {
 struct batmap_set {
     batmap_params params{};
     uint32_t m = 0, n = 0, shift = 0, r0 = 0;
+
+    // number of supports (pairs) the set reports
+    uint64_t npairs() const { return n_a ? (uint64_t)n_a * (n - n_a) : (uint64_t)n * (n > 0 ? n - 1 : 0) / 2; }
     uint64_t n_elements = 0, bytes = 0, n_failed = 0, n_corr = 0;
     double word_pairs = 0.0;
+    uint32_t n_a = 0;            // cross mode: items [0, n_a) x [n_a, n); 0 = all pairs
     uint64_t gen = 0;            // unique build id (batch plans key on it)
     bool skip_schedule = false;  // pool builds need no all-pairs schedule
     cudaStream_t stream = nullptr;

@@ -18,11 +18,12 @@ constexpr int CPER = 16;
 constexpr uint64_t CCHUNK = (uint64_t)CTPB * CPER;
 
 __global__ void k_apply_corrections(const uint32_t *__restrict__ corr, uint64_t ncorr, uint64_t n,
-                                    uint32_t *__restrict__ C) {
+                                    uint32_t n_a, uint32_t *__restrict__ C) {
     for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < ncorr;
          k += (uint64_t)gridDim.x * blockDim.x) {
-        uint64_t i = corr[2 * k], j = corr[2 * k + 1];
-        atomicAdd(&C[i * n - i * (i + 1) / 2 + (j - i - 1)], 1u);
+        const uint32_t i = corr[2 * k], j = corr[2 * k + 1];
+        if (n_a && !(i < n_a && j >= n_a)) continue;  // cross mode: A x B pairs only
+        atomicAdd(&C[support_index(i, j, n, n_a)], 1u);
     }
 }
 
@@ -38,7 +39,7 @@ __device__ __forceinline__ uint64_t row_of(uint64_t L, uint64_t n) {
 }
 
 template <bool WRITE>
-__global__ void k_threshold(const uint32_t *__restrict__ C, uint64_t npairs, uint64_t n, uint32_t s,
+__global__ void k_threshold(const uint32_t *__restrict__ C, uint64_t npairs, uint64_t n, uint32_t n_a, uint32_t s,
                             uint64_t *__restrict__ blocksums, uint32_t *__restrict__ out, uint64_t cap) {
     const uint64_t base = blockIdx.x * CCHUNK;
     uint64_t running = WRITE ? blocksums[blockIdx.x] : 0;
@@ -55,8 +56,14 @@ __global__ void k_threshold(const uint32_t *__restrict__ C, uint64_t npairs, uin
         if (WRITE && keep) {
             uint64_t idx = running + rank;
             if (idx < cap) {
-                uint64_t i = row_of(L, n);
-                uint64_t jj = L - (i * n - i * (i + 1) / 2) + i + 1;
+                uint64_t i, jj;
+                if (n_a) {  // rectangular: (A item, B item numbered from 0)
+                    i = L / (n - n_a);
+                    jj = L - i * (n - n_a);
+                } else {
+                    i = row_of(L, n);
+                    jj = L - (i * n - i * (i + 1) / 2) + i + 1;
+                }
                 out[3 * idx] = (uint32_t)i;
                 out[3 * idx + 1] = (uint32_t)jj;
                 out[3 * idx + 2] = v;
@@ -69,8 +76,7 @@ __global__ void k_threshold(const uint32_t *__restrict__ C, uint64_t npairs, uin
 
 // Allocates the compaction scratch of a set ahead of stream capture.
 void prepare_compaction(batmap_set *S) {
-    const uint64_t n = S->n;
-    const uint64_t npairs = n * (n - 1) / 2;
+    const uint64_t npairs = S->npairs();
     if (npairs) S->d_blocksums.ensure((npairs + CCHUNK - 1) / CCHUNK + 1);
 }
 
@@ -80,10 +86,10 @@ void prepare_compaction(batmap_set *S) {
 void enqueue_correct_compact(batmap_set *S, uint32_t *C, uint32_t s, uint32_t *d_pairs, uint64_t cap,
                              uint64_t *d_total, cudaStream_t st) {
     const uint64_t n = S->n;
-    const uint64_t npairs = n * (n - 1) / 2;
+    const uint64_t npairs = S->npairs();
     if (S->n_corr) {
         uint64_t g = std::min<uint64_t>((S->n_corr + 255) / 256, 1u << 16);
-        k_apply_corrections<<<(unsigned)g, 256, 0, st>>>(S->d_corr.p, S->n_corr, n, C);
+        k_apply_corrections<<<(unsigned)g, 256, 0, st>>>(S->d_corr.p, S->n_corr, n, S->n_a, C);
         BM_CHECK_LAUNCH();
     }
     if (npairs == 0) {
@@ -92,11 +98,11 @@ void enqueue_correct_compact(batmap_set *S, uint32_t *C, uint32_t s, uint32_t *d
     }
     const uint64_t nblk = (npairs + CCHUNK - 1) / CCHUNK;
     prepare_compaction(S);
-    k_threshold<false><<<(unsigned)nblk, CTPB, 0, st>>>(C, npairs, n, s, S->d_blocksums.p, nullptr, 0);
+    k_threshold<false><<<(unsigned)nblk, CTPB, 0, st>>>(C, npairs, n, S->n_a, s, S->d_blocksums.p, nullptr, 0);
     BM_CHECK_LAUNCH();
     scan_exclusive(S->d_blocksums.p, nblk, d_total, st);
     if (cap && d_pairs) {
-        k_threshold<true><<<(unsigned)nblk, CTPB, 0, st>>>(C, npairs, n, s, S->d_blocksums.p, d_pairs, cap);
+        k_threshold<true><<<(unsigned)nblk, CTPB, 0, st>>>(C, npairs, n, S->n_a, s, S->d_blocksums.p, d_pairs, cap);
         BM_CHECK_LAUNCH();
     }
 }
@@ -112,11 +118,11 @@ void enqueue_threshold(uint32_t *C, uint64_t n, uint32_t s, uint32_t *d_pairs, u
     }
     const uint64_t nblk = (npairs + CCHUNK - 1) / CCHUNK;
     blocksums->ensure(nblk + 1);
-    k_threshold<false><<<(unsigned)nblk, CTPB, 0, st>>>(C, npairs, n, s, blocksums->p, nullptr, 0);
+    k_threshold<false><<<(unsigned)nblk, CTPB, 0, st>>>(C, npairs, n, 0, s, blocksums->p, nullptr, 0);
     BM_CHECK_LAUNCH();
     scan_exclusive(blocksums->p, nblk, d_total, st);
     if (cap && d_pairs) {
-        k_threshold<true><<<(unsigned)nblk, CTPB, 0, st>>>(C, npairs, n, s, blocksums->p, d_pairs, cap);
+        k_threshold<true><<<(unsigned)nblk, CTPB, 0, st>>>(C, npairs, n, 0, s, blocksums->p, d_pairs, cap);
         BM_CHECK_LAUNCH();
     }
 }

@@ -205,10 +205,8 @@ __device__ __forceinline__ void process_unit(uint4 *smem, const InstView &V, con
         for (int b = 0; b < MC; b++) {
             const uint32_t gj = wu.c0 + tc + TC_T * b;
             const uint32_t v = acc[a][b] >> 7;
-            if (gj < wu.c1 && gi < gj && v) {
-                const uint32_t oj = __ldg(&V.order[gj]);
-                const uint64_t lo = oi < oj ? oi : oj, hi = oi < oj ? oj : oi;
-                uint32_t *dst = &V.C[lo * n - lo * (lo + 1) / 2 + (hi - lo - 1)];
+            if (gj < wu.c1 && (V.n_a || gi < gj) && v) {
+                uint32_t *dst = &V.C[support_index(oi, __ldg(&V.order[gj]), n, V.n_a)];
                 if (wu.shape & UNIT_WHOLE_K) *dst = v; else atomicAdd(dst, v);
             }
         }
@@ -333,10 +331,8 @@ __device__ __forceinline__ void process_unit_direct(uint4 *smem, const InstView 
         for (int b = 0; b < MC; b++) {
             const uint32_t gj = wu.c0 + tc + TC_T * b;
             const uint32_t v = acc[a][b] >> 7;
-            if (gj < wu.c1 && gi < gj && v) {
-                const uint32_t oj = __ldg(&V.order[gj]);
-                const uint64_t lo = oi < oj ? oi : oj, hi = oi < oj ? oj : oi;
-                uint32_t *dst = &V.C[lo * n - lo * (lo + 1) / 2 + (hi - lo - 1)];
+            if (gj < wu.c1 && (V.n_a || gi < gj) && v) {
+                uint32_t *dst = &V.C[support_index(oi, __ldg(&V.order[gj]), n, V.n_a)];
                 if (wu.shape & UNIT_WHOLE_K) *dst = v; else atomicAdd(dst, v);
             }
         }
@@ -429,11 +425,34 @@ struct Tile2 {
     uint32_t r0, r1, c0, c1;
 };
 
-static void class_tiles(uint32_t cb, uint32_t ce, const ShapeDesc &sh, std::vector<Tile2> *out) {
+// Tiles of the column class [cb, ce).  All pairs: the rows are every earlier
+// item, [0, c1 - 1).  Cross mode: the rows are the given range of the other
+// family (items no wider than the columns).
+static void class_tiles(uint32_t cb, uint32_t ce, const ShapeDesc &sh, std::vector<Tile2> *out,
+                        bool cross = false, uint32_t row_lo = 0, uint32_t row_hi = 0) {
     for (uint32_t c0 = cb; c0 < ce; c0 += sh.TC) {
         uint32_t c1 = std::min(ce, c0 + sh.TC);
-        uint32_t rows = c1 - 1;  // rows [0, c1 - 1) pair with some column of the block
-        for (uint32_t r0 = 0; r0 < rows; r0 += sh.TR) out->push_back({r0, std::min(rows, r0 + sh.TR), c0, c1});
+        uint32_t lo = cross ? row_lo : 0, hi = cross ? row_hi : c1 - 1;
+        for (uint32_t r0 = lo; r0 < hi; r0 += sh.TR) out->push_back({r0, std::min(hi, r0 + sh.TR), c0, c1});
+    }
+}
+
+// Cross mode, items sorted family first then by width: rows for a column
+// class in family B are the A items with width <= the class width; for a
+// class in family A, the B items strictly narrower (equal widths are taken
+// once, from the B side).
+static void cross_rows(const batmap_set *S, uint32_t cb, uint32_t *lo, uint32_t *hi) {
+    const uint32_t e = S->wshift_sorted[cb];
+    if (cb >= S->n_a) {
+        uint32_t r = 0;
+        while (r < S->n_a && S->wshift_sorted[r] <= e) r++;
+        *lo = 0;
+        *hi = r;
+    } else {
+        uint32_t r = S->n_a;
+        while (r < S->n && S->wshift_sorted[r] < e) r++;
+        *lo = S->n_a;
+        *hi = r;
     }
 }
 
@@ -457,7 +476,13 @@ void schedule_units(const batmap_set *S, uint32_t force_shape, const double *sha
             if (!force_shape && S->params.shape_mask && !((S->params.shape_mask >> s) & 1u)) continue;
             if (K % SHAPES[s].KC) continue;
             std::vector<Tile2> tiles;
-            class_tiles(cb, ce, SHAPES[s], &tiles);
+            if (S->n_a) {
+                uint32_t lo, hi;
+                cross_rows(S, cb, &lo, &hi);
+                class_tiles(cb, ce, SHAPES[s], &tiles, true, lo, hi);
+            } else {
+                class_tiles(cb, ce, SHAPES[s], &tiles);
+            }
             double cost = (double)tiles.size() * SHAPES[s].TR * SHAPES[s].TC * (double)K /
                           (shape_eff ? shape_eff[s] : SHAPES[s].eff);
             if (cost < best_cost) {
