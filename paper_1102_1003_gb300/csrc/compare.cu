@@ -65,9 +65,11 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, bool v
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src),
                  "r"(valid ? 16 : 0));
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// The memory clobber keeps the compiler from moving shared-memory reads of the
+// copied data above the wait.
 template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 __device__ __forceinline__ uint32_t wrap_word(uint32_t k, uint32_t e) {
     uint32_t q = k >> e;
@@ -213,26 +215,42 @@ __device__ __forceinline__ void process_unit(uint4 *smem, const InstView &V, con
     }
 }
 
-// Register-streaming variant: every thread streams its own 8 row chunks per
-// 4-word step into a private 4-deep shared-memory ring with cp.async (it
-// waits only for its own copy groups: no block barrier) and loads its MC
-// column words straight from global memory (128-bit loads through L1; lanes
-// that share a column are served by one request).  Suited to narrow column
-// tiles, where a staged row word has only a few partners.  The wrap of a
-// narrower row is an incremental index reset.
-// Per-thread ring depth of the register-streaming path (16-byte row chunks
-// prefetched DEPTH-1 steps ahead).
-constexpr int DIRECT_DEPTH = 4;
+// Register-streaming variant for narrow column tiles, where a staged row word
+// would have only a few partners.  Every thread streams its own MR row chunks
+// per 4-word step into a private DEPTH-deep shared-memory ring with cp.async
+// and waits only for its own copy groups.  The tile's TC column chunks are
+// staged COL_CK steps at a time into a COL_STAGES-deep shared ring (laid out
+// [step][column], so the TC_T distinct columns a warp reads are adjacent and
+// conflict-free); one block barrier per COL_CK steps publishes a column stage
+// and frees the oldest.  The wrap of a narrower row is an incremental index
+// reset.
+constexpr int DIRECT_DEPTH = 4;  // per-thread row ring (16-byte chunks, DEPTH-1 steps ahead)
+constexpr int COL_CK = 8;        // column chunks per stage (32 words)
+constexpr int COL_STAGES = 3;    // column stages in flight
+static_assert(2 * COL_CK >= DIRECT_DEPTH, "column copies must retire before their stage is read");
 
-template <int TR_T, int TC_T, int MC, int MR = 8>
+template <int TR_T, int TC_T, int MC, int MR, bool STAGE_COLS>
+struct DirectTile {
+    static constexpr int TC = TC_T * MC;
+    static constexpr int ROW_CHUNKS = DIRECT_DEPTH * MR * 256;
+    static constexpr int COL_STAGE = COL_CK * TC;
+    static constexpr int FILL = STAGE_COLS ? (COL_STAGE + 255) / 256 : 1;  // column chunks copied per thread
+    // the dynamic shared memory of the kernel is the maximum over shapes and
+    // is taken from L1, which the unstaged column loads go through
+    static constexpr size_t SMEM = (size_t)(ROW_CHUNKS + (STAGE_COLS ? COL_STAGES * COL_STAGE : 0)) * 16;
+};
+
+template <int TR_T, int TC_T, int MC, int MR, bool STAGE_COLS>
 __device__ __forceinline__ void process_unit_direct(uint4 *smem, const InstView &V, const WorkUnit &wu) {
+    using T = DirectTile<TR_T, TC_T, MC, MR, STAGE_COLS>;
     const int tid = threadIdx.x;
     const int tc = tid % TC_T;
     const int tr = tid / TC_T;
     const uint32_t q0 = wu.k0 >> 2;  // first 16-byte chunk of the column range
     const uint32_t nq = wu.klen >> 2;
-    const uint4 zero = make_uint4(0, 0, 0, 0);
+    const uint32_t nstage = (nq + COL_CK - 1) / COL_CK;
     const uint4 *__restrict__ bm = V.bm;
+    uint4 *const cring = smem + T::ROW_CHUNKS;
 
     // row state: chunk index of the row start, current chunk, row length (chunks)
     uint32_t rbase[MR], rcur[MR], rlen[MR];
@@ -250,12 +268,36 @@ __device__ __forceinline__ void process_unit_direct(uint4 *smem, const InstView 
             rcur[a] = 0;
         }
     }
+    // the column chunks this thread copies in every stage: slot f = tid + 256 i
+    // holds (step f / TC, tile column f % TC)
+    uint32_t fbase[T::FILL];
+#pragma unroll
+    for (int i = 0; i < T::FILL; i++) {
+        const uint32_t f = tid + 256u * i, c = f % T::TC;
+        fbase[i] = (STAGE_COLS && f < (uint32_t)T::COL_STAGE && wu.c0 + c < wu.c1)
+                       ? __ldg(&V.line_off[wu.c0 + c]) * 8u + q0
+                       : 0xFFFFFFFFu;
+    }
+    // without column staging: the thread's own column chunks, loaded from
+    // global memory (through L1) one step ahead into registers
     uint32_t cbase[MC];
 #pragma unroll
     for (int b = 0; b < MC; b++) {
         const uint32_t g = wu.c0 + tc + TC_T * b;
-        cbase[b] = g < wu.c1 ? __ldg(&V.line_off[g]) * 8u + q0 : 0xFFFFFFFFu;
+        cbase[b] = (!STAGE_COLS && g < wu.c1) ? __ldg(&V.line_off[g]) * 8u + q0 : 0xFFFFFFFFu;
     }
+    auto fill_cols = [&](uint32_t st) {
+#pragma unroll
+        for (int i = 0; i < T::FILL; i++) {
+            const uint32_t f = tid + 256u * i;
+            if (f < (uint32_t)T::COL_STAGE) {
+                const uint32_t q = st * COL_CK + f / T::TC;
+                const bool ok = fbase[i] != 0xFFFFFFFFu && q < nq;
+                cp_async16(smem_u32(cring + (st % COL_STAGES) * T::COL_STAGE + f),
+                           ok ? (const void *)(bm + (size_t)fbase[i] + q) : (const void *)bm, ok);
+            }
+        }
+    };
 
     uint32_t acc[MR][MC];
 #pragma unroll
@@ -263,8 +305,6 @@ __device__ __forceinline__ void process_unit_direct(uint4 *smem, const InstView 
 #pragma unroll
         for (int b = 0; b < MC; b++) acc[a][b] = 0;
 
-    // Each thread copies its own row chunks into a private ring slot
-    // ring[(step % DEPTH) * MR + a][tid] and waits only for its own copy groups.
     auto issue_rows = [&](uint32_t step) {
         uint4 *slot = smem + (size_t)(step % DIRECT_DEPTH) * MR * 256 + tid;
 #pragma unroll
@@ -275,26 +315,55 @@ __device__ __forceinline__ void process_unit_direct(uint4 *smem, const InstView 
             rcur[a] = (rcur[a] + 1 == rlen[a]) ? 0 : rcur[a] + 1;
         }
     };
+    // Copy groups: the prologue commits DEPTH-1 groups (the first also holds
+    // column stages 0 .. COL_STAGES-2); step q commits one group (rows of step
+    // q+DEPTH-1, plus column stage s+COL_STAGES-1 when q = s*COL_CK).  Waiting
+    // until DEPTH-1 groups are pending retires the rows of step q and every
+    // column stage issued at least 2*COL_CK >= DEPTH steps earlier.
+    if constexpr (STAGE_COLS) {
+#pragma unroll
+        for (int st = 0; st < COL_STAGES - 1; st++)
+            if ((uint32_t)st < nstage) fill_cols(st);
+    }
 #pragma unroll
     for (int d = 0; d < DIRECT_DEPTH - 1; d++) {
         if ((uint32_t)d < nq) issue_rows(d);
         cp_async_commit();
     }
 
-    // column chunks are loaded one step ahead into registers
+    const uint4 zero = make_uint4(0, 0, 0, 0);
     uint4 Y[MC];
+    if constexpr (!STAGE_COLS) {
 #pragma unroll
-    for (int b = 0; b < MC; b++) Y[b] = (cbase[b] != 0xFFFFFFFFu && nq) ? __ldg(bm + (size_t)cbase[b]) : zero;
+        for (int b = 0; b < MC; b++) Y[b] = (cbase[b] != 0xFFFFFFFFu && nq) ? __ldg(bm + (size_t)cbase[b]) : zero;
+    }
 
 #pragma unroll 1
     for (uint32_t q = 0; q < nq; q++) {
+        if constexpr (STAGE_COLS) {
+            // waiting with DEPTH-2 groups pending before this step's commit is
+            // the same retirement point as DEPTH-1 after it
+            const uint32_t s = q / COL_CK, kq = q % COL_CK;
+            if (kq == 0) {
+                cp_async_wait<DIRECT_DEPTH - 2>();
+                __syncthreads();  // column stage s is complete; stage s-1 is no longer read
+                if (s + COL_STAGES - 1 < nstage) fill_cols(s + COL_STAGES - 1);
+            }
+            // the column words are read before the row copies are issued, so
+            // their latency overlaps the copy issue and the wait
+            const uint4 *cs = cring + (s % COL_STAGES) * T::COL_STAGE + kq * T::TC + tc;
+#pragma unroll
+            for (int b = 0; b < MC; b++) Y[b] = cs[TC_T * b];
+        }
         if (q + DIRECT_DEPTH - 1 < nq) issue_rows(q + DIRECT_DEPTH - 1);
         cp_async_commit();
         uint4 Yn[MC];
-        const bool more = q + 1 < nq;
+        if constexpr (!STAGE_COLS) {
+            const bool more = q + 1 < nq;
 #pragma unroll
-        for (int b = 0; b < MC; b++)
-            Yn[b] = (more && cbase[b] != 0xFFFFFFFFu) ? __ldg(bm + (size_t)cbase[b] + q + 1) : zero;
+            for (int b = 0; b < MC; b++)
+                Yn[b] = (more && cbase[b] != 0xFFFFFFFFu) ? __ldg(bm + (size_t)cbase[b] + q + 1) : zero;
+        }
         cp_async_wait<DIRECT_DEPTH - 1>();
         uint4 X[MR];
         const uint4 *slot = smem + (size_t)(q % DIRECT_DEPTH) * MR * 256 + tid;
@@ -316,8 +385,10 @@ __device__ __forceinline__ void process_unit_direct(uint4 *smem, const InstView 
                 for (int b = 0; b < MC; b++) acc[a][b] = swar_step(acc[a][b], xw, xi, yw[b], yi[b]);
             }
         }
+        if constexpr (!STAGE_COLS) {
 #pragma unroll
-        for (int b = 0; b < MC; b++) Y[b] = Yn[b];
+            for (int b = 0; b < MC; b++) Y[b] = Yn[b];
+        }
     }
     cp_async_wait<0>();
 
@@ -347,14 +418,14 @@ __device__ __forceinline__ void process_unit_direct(uint4 *smem, const InstView 
     X(4, 256, 1, 8, 8, 2)         \
     X(5, 256, 1, 4, 8, 2)
 
-#define BM_DIRECT_LIST(X) \
-    X(6, 16, 16, 8, 8)      \
-    X(7, 32, 8, 8, 8)       \
-    X(8, 64, 4, 8, 8)       \
-    X(9, 128, 2, 8, 8)      \
-    X(10, 256, 1, 8, 8)     \
-    X(11, 256, 1, 4, 8)     \
-    X(12, 256, 1, 12, 4)
+#define BM_DIRECT_LIST(X)      \
+    X(6, 16, 16, 8, 8, false)    \
+    X(7, 32, 8, 8, 8, false)     \
+    X(8, 64, 4, 8, 8, false)     \
+    X(9, 128, 2, 8, 8, false)    \
+    X(10, 256, 1, 8, 8, false)   \
+    X(11, 256, 1, 4, 8, false)   \
+    X(12, 256, 1, 12, 4, true)
 
 size_t compare_smem_bytes(uint32_t shape_idx) {
 #define X(i, a, b, c, d, e) if (shape_idx == i) return Tile<a, b, c, d, e>::SMEM;
@@ -364,7 +435,10 @@ size_t compare_smem_bytes(uint32_t shape_idx) {
 }
 
 static size_t max_smem_bytes() {
-    size_t m = (size_t)DIRECT_DEPTH * 8 * 256 * sizeof(uint4);  // register-streaming ring
+    size_t m = 0;
+#define X(i, a, b, c, d, e) m = std::max(m, DirectTile<a, b, c, d, e>::SMEM);
+    BM_DIRECT_LIST(X)
+#undef X
     for (uint32_t s = 0; s < NUM_SHAPES; s++) m = std::max(m, compare_smem_bytes(s));
     return m;
 }
@@ -388,7 +462,7 @@ k_compare(const InstView *__restrict__ views, const WorkUnit *__restrict__ units
 #define X(i, a, b, c, d, e) case i: process_unit<a, b, c, d, e>(smem, V, wu); break;
             BM_SHAPE_LIST(X)
 #undef X
-#define X(i, a, b, c, d) case i: process_unit_direct<a, b, c, d>(smem, V, wu); break;
+#define X(i, a, b, c, d, e) case i: process_unit_direct<a, b, c, d, e>(smem, V, wu); break;
             BM_DIRECT_LIST(X)
 #undef X
             default: break;
