@@ -134,10 +134,11 @@ def transactions_to_tidlists(transactions, m: int, n: int) -> Instance:
     return from_lists([sorted(set(l)) for l in lists], m)
 
 
-def permutations(m: int, seed: int) -> np.ndarray:
-    """The three random permutations pi_1..pi_3 of [0, m) (Sec. III-A), uint32[3, m]."""
-    out = np.empty((3, max(m, 0)), dtype=np.uint32)
-    for t in range(3):
+def permutations(m: int, seed: int, count: int = 3) -> np.ndarray:
+    """The random permutations pi_1..pi_count of [0, m) (Sec. III-A: three; a
+    d-of-(d+1) BatMap uses d+1), uint32[count, m]; row t does not depend on count."""
+    out = np.empty((count, max(m, 0)), dtype=np.uint32)
+    for t in range(count):
         out[t] = np.random.default_rng([int(seed), 0xB47, t]).permutation(m).astype(np.uint32)
     return out
 

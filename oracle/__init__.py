@@ -7,7 +7,9 @@ arm may import this package.  It shares no code with the CUDA path.
 this module loads it with ctypes, compiling it with gcc on first use when no
 built copy exists.  `batmap_rules` restates the paper's BatMap rules on the
 CPU (sizing, layout hash, 8-bit codes, indicator bits, counting rule, the
-serial INSERT procedure) for pins and for checking layouts built on the GPU.
+serial INSERT procedure) for pins and for checking layouts built on the GPU;
+`dof_rules` does the same for the d-of-(d+1) generalisation of Sec. V and holds
+the Apriori candidate step for itemsets of size 3.
 """
 from __future__ import annotations
 
