@@ -92,6 +92,8 @@ typedef struct batmap_info {
     uint32_t n_classes;      /* distinct BatMap widths                         */
     uint32_t n_a;            /* cross mode: size of family A (0 = all pairs)    */
     double word_pairs;       /* sum over reported pairs of max(|B_i|,|B_j|)/4  */
+    uint32_t d;              /* copies per element: 2 (2-of-3) or 3 (3-of-4)   */
+    uint32_t reserved;
 } batmap_info;
 
 /* Fills *p with the defaults documented above. */
@@ -140,6 +142,62 @@ batmap_status batmap_build(const batmap_params *p, uint32_t m, uint32_t n,
 batmap_status batmap_build_cross(const batmap_params *p, uint32_t m, uint32_t n_a, uint32_t n_b,
                                  const uint64_t *d_offsets, const uint32_t *d_tids, const uint32_t *d_perm,
                                  cudaStream_t stream, batmap_set **out);
+
+/*
+ * d-of-(d+1) BatMaps, the generalisation that closes Sec. V: every element is
+ * kept in d of d+1 hashed tables, so the sets of any itemset of size up to d
+ * share a table that witnesses each common element.  d = 2 is batmap_build
+ * (the paper's 2-of-3 format; all pair calls apply).  d = 3 builds 3-of-4
+ * BatMaps for k-way supports (itemset_support, frequent_triples only):
+ *   width 4 r_i bytes (four tables interleaved in blocks of r_0), slot
+ *   h_t(x) = 4 r_0 floor((pi_t(x) mod r_i)/r_0) + (pi_t(x) mod r_0) + t r_0,
+ *   byte = (missing table << 6) | ((pi_t(x) >> s) + 1), 0x00 empty, s the
+ *   smallest shift >= min_shift with m <= 63 * 2^s; elements left with fewer
+ *   than three copies are failed insertions (F_i), corrected exactly.
+ *   d_perm : device uint32[(d+1) * m], rows pi_0 .. pi_d (the library keeps a
+ *            copy for d = 3).  Other arguments as batmap_build.
+ * Items keep their original order (no width sort); h_bytes of
+ * batmap_export_layout follow it.  Errors: BATMAP_ERR_ARG for d outside
+ * {2, 3} or invalid input.
+ */
+batmap_status batmap_build_d(const batmap_params *p, uint32_t d, uint32_t m, uint32_t n,
+                             const uint64_t *d_offsets, const uint32_t *d_tids, const uint32_t *d_perm,
+                             cudaStream_t stream, batmap_set **out);
+
+/*
+ * |S_a1 ∩ ... ∩ S_ak| for n_q queries of k item ids (k = 1, 2 or 3) on a set
+ * built with d = 3, by the witness rule: the slot of table t counts iff the
+ * six code bits of the k bytes agree and are nonzero and t is the smallest
+ * table missed by none of the k sets (read from the bytes' top two bits);
+ * failed common elements are added from the F lists.
+ *   d_items   : device uint32[k * n_q], query q = d_items[k q .. k q + k),
+ *               ids < n (checked; repeats allowed).
+ *   d_support : device uint32[n_q] (written).
+ * Asynchronous apart from the id check (one stream synchronisation).
+ * Errors: BATMAP_ERR_ARG (d != 3, k out of range, id >= n, NULL pointer).
+ */
+batmap_status itemset_support(batmap_set *set, uint32_t k, uint64_t n_q, const uint32_t *d_items,
+                              uint32_t *d_support, cudaStream_t stream);
+
+/*
+ * Frequent itemsets of size 3 (the problem of Sec. I beyond pairs): the
+ * Apriori join-and-prune step turns the frequent pairs into the candidates
+ * {a < b < c} whose three 2-subsets are all frequent, itemset_support counts
+ * them on the 3-of-4 set, and those with support >= s are written.
+ *   d_pairs : device uint32[3 * n_pairs], (i, j, support) with i < j < n in
+ *             lexicographic order: the output of pair_support_all for the
+ *             same tidlists and threshold s (checked: order and ids).
+ *   d_out   : device uint32[4 * cap], (a, b, c, support), lexicographic.
+ *   n_out   : host, number of frequent triples (all of them, even > cap).
+ *   n_candidates : host, may be NULL; number of candidates counted.
+ * Synchronises `stream`.  Timing: compare_ms = the support kernel,
+ * compact_ms = candidate generation + compaction, pairs_ms = the call.
+ * Errors: BATMAP_ERR_ARG, BATMAP_ERR_CAPACITY (cap < *n_out; the first cap
+ * triples are written).
+ */
+batmap_status frequent_triples(batmap_set *set, uint32_t s, const uint32_t *d_pairs, uint64_t n_pairs,
+                               uint32_t *d_out, uint64_t cap, uint64_t *n_out, uint64_t *n_candidates,
+                               cudaStream_t stream);
 
 /* Release a handle and all device memory it owns (NULL is ignored). */
 void batmap_free(batmap_set *set);

@@ -29,6 +29,7 @@ EXPORTED = [
     "pair_support_batch", "batmap_get_timing", "batmap_kernel_launches", "pair_threshold_noalloc",
     "pair_support_dense", "batmap_pool_create", "batmap_pool_free", "batmap_pool_info", "intersect_query",
     "batmap_serve", "batmap_autotune", "batmap_release_scratch", "intersect_query_list", "batmap_build_cross",
+    "batmap_build_d", "itemset_support", "frequent_triples",
 ]
 
 
@@ -45,7 +46,7 @@ class batmap_info(ctypes.Structure):
                 ("n_elements", ctypes.c_uint64), ("n_failed", ctypes.c_uint64),
                 ("n_corrections", ctypes.c_uint64), ("n_work_units", ctypes.c_uint64),
                 ("n_classes", ctypes.c_uint32), ("n_a", ctypes.c_uint32),
-                ("word_pairs", ctypes.c_double)]
+                ("word_pairs", ctypes.c_double), ("d", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -148,6 +149,12 @@ def load_library(path: str = LIB_PATH):
     L.batmap_autotune.restype = ctypes.c_int
     L.pair_threshold_noalloc.argtypes = [vp, u32, u32, vp, u64, ctypes.POINTER(u64), vp]
     L.pair_threshold_noalloc.restype = ctypes.c_int
+    L.batmap_build_d.argtypes = [ctypes.POINTER(batmap_params), u32, u32, u32, vp, vp, vp, vp, ctypes.POINTER(vp)]
+    L.batmap_build_d.restype = ctypes.c_int
+    L.itemset_support.argtypes = [vp, u32, u64, vp, vp, vp]
+    L.itemset_support.restype = ctypes.c_int
+    L.frequent_triples.argtypes = [vp, u32, vp, u64, vp, u64, ctypes.POINTER(u64), ctypes.POINTER(u64), vp]
+    L.frequent_triples.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -226,6 +233,58 @@ def batmap_build_cross(m: int, n_a: int, offsets, tids, perm, params: batmap_par
     b = BatMapSet(h, int(m), n)
     b.n_a = int(n_a)
     return b
+
+
+def batmap_build_d(d: int, m: int, offsets, tids, perm, params: batmap_params | None = None,
+                   stream=None) -> BatMapSet:
+    """d-of-(d+1) BatMaps (Sec. V generalisation): d = 2 is batmap_build; d = 3 builds
+    3-of-4 BatMaps for itemset_support / frequent_triples.  perm: cuda [d+1, m]."""
+    L = load_library()
+    n = int(offsets.numel()) - 1
+    if d in (2, 3) and int(perm.numel()) != (d + 1) * int(m):
+        raise ValueError(f"perm must hold {d + 1} rows of m = {m} entries")
+    h = ctypes.c_void_p()
+    pp = ctypes.byref(params) if params is not None else None
+    _check(L.batmap_build_d(pp, int(d), int(m), n, _ptr(offsets), _ptr(tids) if tids.numel() else None,
+                            _ptr(perm), _stream_handle(stream), ctypes.byref(h)))
+    b = BatMapSet(h, int(m), n)
+    b.d = int(d)
+    return b
+
+
+def itemset_support(bset: BatMapSet, items, support=None, stream=None):
+    """|S_a1 cap ... cap S_ak| for a cuda int32 tensor items [n_q, k] (k <= 3) on a
+    3-of-4 set; returns the cuda int32 [n_q] supports."""
+    import torch
+    nq, k = int(items.shape[0]), int(items.shape[1])
+    if support is None:
+        support = torch.empty(max(nq, 1), dtype=torch.int32, device=items.device)
+    _check(load_library().itemset_support(bset.handle, k, nq, _ptr(items) if nq else None,
+                                          _ptr(support), _stream_handle(stream)))
+    return support[:nq]
+
+
+def frequent_triples(bset: BatMapSet, s: int, pairs, out=None, stream=None):
+    """Frequent itemsets of size 3 from the frequent pairs (cuda int32 [k, 3], the
+    output of pair_support_all with the same s); returns (n_out, triples view
+    [min(n_out, cap), 4] of (a, b, c, support), n_candidates)."""
+    import torch
+    L = load_library()
+    np_ = int(pairs.shape[0])
+    n_out, n_cand = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    st = _stream_handle(stream)
+    pp = _ptr(pairs) if np_ else None
+    if out is None:
+        rc = L.frequent_triples(bset.handle, int(s), pp, np_, None, 0, ctypes.byref(n_out),
+                                ctypes.byref(n_cand), st)
+        _check(rc, allow=(BATMAP_ERR_CAPACITY,))
+        out = torch.empty((max(int(n_out.value), 1), 4), dtype=torch.int32, device="cuda")
+    cap = out.numel() // 4
+    rc = L.frequent_triples(bset.handle, int(s), pp, np_, _ptr(out), cap, ctypes.byref(n_out),
+                            ctypes.byref(n_cand), st)
+    _check(rc, allow=(BATMAP_ERR_CAPACITY,))
+    k = min(int(n_out.value), cap)
+    return int(n_out.value), out.view(-1, 4)[:k], int(n_cand.value)
 
 
 def batmap_free(bset: BatMapSet):

@@ -15,36 +15,12 @@
 #include <numeric>
 
 #include "common.cuh"
+#include "items.cuh"
 #include "scan.cuh"
 
 namespace bm {
 
-constexpr uint32_t EMPTY = 0xFFFFFFFFu;
-constexpr int TPB = 256;
-constexpr int PER_THREAD = 16;
-constexpr int CHUNK = TPB * PER_THREAD;  // elements handled by one block
-
 void build_schedule(batmap_set *S);  // compare.cu
-
-// Per-item view for the element kernels (original item order).
-struct ItemView {
-    const uint64_t *off;     // CSR offsets [n+1]
-    const uint32_t *tids;    // CSR tids
-    const uint64_t *base;    // [n] first slot (byte) of item i in the BatMap array
-    const uint32_t *rlog;    // [n] log2 r_i
-    const uint32_t *ch_item; // [chunks] item of chunk b
-    const uint64_t *ch_start;// [chunks] first element of chunk b
-};
-
-__device__ __forceinline__ void chunk_range(const ItemView &v, uint32_t b, uint32_t *item,
-                                            uint64_t *e0, uint64_t *e1) {
-    uint32_t i = v.ch_item[b];
-    uint64_t s = v.ch_start[b];
-    uint64_t end = v.off[i + 1];
-    *item = i;
-    *e0 = s;
-    *e1 = s + CHUNK < end ? s + CHUNK : end;
-}
 
 // ---- validation ---------------------------------------------------------------
 
@@ -60,8 +36,8 @@ __global__ void k_validate_tids(ItemView v, uint32_t m, int *err) {
     }
 }
 
-__global__ void k_validate_perm(const uint32_t *perm, uint32_t m, uint32_t *bits, int *err) {
-    uint64_t total = 3ull * m;
+__global__ void k_validate_perm(const uint32_t *perm, uint32_t m, uint32_t rows, uint32_t *bits, int *err) {
+    uint64_t total = (uint64_t)rows * m;
     for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < total;
          q += (uint64_t)gridDim.x * blockDim.x) {
         uint32_t t = (uint32_t)(q / m);
@@ -298,26 +274,14 @@ static uint32_t shift_bits(uint32_t m, uint32_t min_shift) {
     return s;
 }
 
-static uint32_t log2_range(uint64_t size, uint32_t num, uint32_t den, uint32_t shift) {
-    uint64_t need = (num * std::max<uint64_t>(size, 1) + den - 1) / den;
-    uint32_t lg = 0;
-    while ((1ull << lg) < need) lg++;
-    return std::max(lg, shift);
-}
-
-static unsigned grid_for(uint64_t work, unsigned tpb = 256) {
-    uint64_t g = (work + tpb - 1) / tpb;
-    return (unsigned)std::min<uint64_t>(std::max<uint64_t>(g, 1), 1u << 20);
-}
-
 // The placement scratch (one uint32 per BatMap byte) is kept between builds
 // so that repeated builds do not pay for allocating and freeing it; it is
 // released when a build needs less than a quarter of it or on
 // batmap_release_scratch().  Builds are serialised on it.
-static std::mutex g_scratch_mu;
+std::mutex g_scratch_mu;
 static DevBuf<uint32_t> g_scratch;
 
-static DevBuf<uint32_t> &scratch_table(uint64_t slots) {
+DevBuf<uint32_t> &scratch_table(uint64_t slots) {
     if (g_scratch.n < slots || g_scratch.n > 4 * slots + (1u << 20)) g_scratch.alloc(slots);
     return g_scratch;
 }
@@ -460,7 +424,7 @@ void build_set(batmap_set *S, const uint64_t *d_offsets, const uint32_t *d_tids,
         BM_CUDA(cudaMemsetAsync(d_bits.p, 0, d_bits.bytes(), st));
         k_validate_tids<<<nch, TPB, 0, st>>>(v, m, d_err.p);
         BM_CHECK_LAUNCH();
-        k_validate_perm<<<grid_for(3ull * m), 256, 0, st>>>(d_perm, m, d_bits.p, d_err.p);
+        k_validate_perm<<<grid_for(3ull * m), 256, 0, st>>>(d_perm, m, 3, d_bits.p, d_err.p);
         BM_CHECK_LAUNCH();
         int err = 0;
         BM_CUDA(cudaMemcpyAsync(&err, d_err.p, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -17,6 +17,11 @@ void set_error(const std::string &msg) { g_last_error = msg; }
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void build_set(batmap_set *S, const uint64_t *d_offsets, const uint32_t *d_tids, const uint32_t *d_perm);
+void build_witness_set(batmap_set *S, const uint64_t *d_offsets, const uint32_t *d_tids, const uint32_t *d_perm);
+void witness_support(batmap_set *S, uint32_t k, uint64_t nq, const uint32_t *d_items, uint32_t *d_support,
+                     cudaStream_t st);
+void frequent_triples(batmap_set *S, uint32_t s, const uint32_t *d_pairs, uint64_t np, uint32_t *d_out,
+                      uint64_t cap, uint64_t *n_out, uint64_t *n_cand, cudaStream_t st);
 void enqueue_correct_compact(batmap_set *S, uint32_t *C, uint32_t s, uint32_t *d_pairs, uint64_t cap,
                              uint64_t *d_total, cudaStream_t st);
 void run_batch(batmap_set *const *sets, const uint32_t *s, uint32_t k, batmap_out *outs, cudaStream_t st);
@@ -79,7 +84,7 @@ const char *batmap_last_error(void) { return g_last_error.c_str(); }
 
 static batmap_status build_any(const batmap_params *p, uint32_t m, uint32_t n, uint32_t n_a,
                                const uint64_t *d_offsets, const uint32_t *d_tids, const uint32_t *d_perm,
-                               cudaStream_t stream, batmap_set **out) {
+                               cudaStream_t stream, batmap_set **out, uint32_t d = 2) {
     return guarded([&] {
         BM_REQUIRE(out != nullptr, BATMAP_ERR_ARG, "out is NULL");
         *out = nullptr;
@@ -98,9 +103,11 @@ static batmap_status build_any(const batmap_params *p, uint32_t m, uint32_t n, u
         S->n = n;
         S->stream = stream;
         S->n_a = n_a;
+        S->d = d;
         S->gen = g_gen.fetch_add(1);
         try {
-            build_set(S, d_offsets, d_tids, d_perm);
+            if (d == 3) build_witness_set(S, d_offsets, d_tids, d_perm);
+            else build_set(S, d_offsets, d_tids, d_perm);
         } catch (...) {
             delete S;
             throw;
@@ -129,6 +136,27 @@ batmap_status batmap_build_cross(const batmap_params *p, uint32_t m, uint32_t n_
     return build_any(p, m, n_a + n_b, n_a, d_offsets, d_tids, d_perm, stream, out);
 }
 
+batmap_status batmap_build_d(const batmap_params *p, uint32_t d, uint32_t m, uint32_t n,
+                             const uint64_t *d_offsets, const uint32_t *d_tids, const uint32_t *d_perm,
+                             cudaStream_t stream, batmap_set **out) {
+    if (d != 2 && d != 3) {
+        set_error("d must be 2 or 3");
+        return BATMAP_ERR_ARG;
+    }
+    return build_any(p, m, n, 0, d_offsets, d_tids, d_perm, stream, out, d);
+}
+
+batmap_status itemset_support(batmap_set *S, uint32_t k, uint64_t n_q, const uint32_t *d_items,
+                              uint32_t *d_support, cudaStream_t st) {
+    return guarded([&] { witness_support(S, k, n_q, d_items, d_support, st); });
+}
+
+batmap_status frequent_triples(batmap_set *S, uint32_t s, const uint32_t *d_pairs, uint64_t n_pairs,
+                               uint32_t *d_out, uint64_t cap, uint64_t *n_out, uint64_t *n_candidates,
+                               cudaStream_t st) {
+    return guarded([&] { bm::frequent_triples(S, s, d_pairs, n_pairs, d_out, cap, n_out, n_candidates, st); });
+}
+
 void batmap_free(batmap_set *set) {
     if (!set) return;
     cudaStreamSynchronize(set->stream);
@@ -152,6 +180,7 @@ batmap_status batmap_get_info(const batmap_set *S, batmap_info *info) {
         info->n_classes = S->class_begin.empty() ? 0 : (uint32_t)S->class_begin.size() - 1;
         info->n_a = S->n_a;
         info->word_pairs = S->word_pairs;
+        info->d = S->d;
     });
 }
 
@@ -179,9 +208,9 @@ batmap_status batmap_export_layout(const batmap_set *S, uint8_t *h_bytes, uint64
 static void pair_support_impl(batmap_set *S, uint32_t s, uint32_t *d_pairs, uint64_t cap,
                               uint64_t *n_out, uint32_t *d_full, cudaStream_t st) {
     BM_REQUIRE(S, BATMAP_ERR_ARG, "NULL set");
+    BM_REQUIRE(S->d == 2, BATMAP_ERR_ARG, "pair calls need a 2-of-3 set (built with d = 2)");
     BM_REQUIRE(n_out, BATMAP_ERR_ARG, "n_out is NULL");
     BM_REQUIRE(cap == 0 || d_pairs, BATMAP_ERR_ARG, "d_pairs is NULL with cap > 0");
-    const uint64_t n = S->n;
     const uint64_t npairs = S->npairs();
     uint32_t *C = d_full;
     if (!C) {
@@ -267,13 +296,25 @@ void batmap_release_scratch(void) {
     release_dense_workspace();
 }
 
+static void require_pair_sets(batmap_set *const *sets, uint32_t k) {
+    BM_REQUIRE(k == 0 || sets, BATMAP_ERR_ARG, "sets is NULL");
+    for (uint32_t i = 0; i < k; i++)
+        BM_REQUIRE(sets[i] && sets[i]->d == 2, BATMAP_ERR_ARG, "pair calls need 2-of-3 sets (built with d = 2)");
+}
+
 batmap_status batmap_autotune(batmap_set *const *sets, uint32_t k, double *shape_eff, cudaStream_t st) {
-    return guarded([&] { autotune(sets, k, shape_eff, st); });
+    return guarded([&] {
+        require_pair_sets(sets, k);
+        autotune(sets, k, shape_eff, st);
+    });
 }
 
 batmap_status pair_support_batch(batmap_set *const *sets, const uint32_t *s, uint32_t k, batmap_out *outs,
                                  cudaStream_t st) {
-    return guarded([&] { run_batch(sets, s, k, outs, st); });
+    return guarded([&] {
+        require_pair_sets(sets, k);
+        run_batch(sets, s, k, outs, st);
+    });
 }
 
 }  // extern "C"

@@ -160,6 +160,7 @@ struct batmap_set {
     uint64_t n_elements = 0, bytes = 0, n_failed = 0, n_corr = 0;
     double word_pairs = 0.0;
     uint32_t n_a = 0;            // cross mode: items [0, n_a) x [n_a, n); 0 = all pairs
+    uint32_t d = 2;              // copies per element: 2 (2-of-3 BatMaps) or 3 (3-of-4, k-way witnesses)
     uint64_t gen = 0;            // unique build id (batch plans key on it)
     bool skip_schedule = false;  // pool builds need no all-pairs schedule
     cudaStream_t stream = nullptr;
@@ -182,6 +183,10 @@ struct batmap_set {
     bm::DevBuf<uint32_t> d_corr;          // [2 * n_corr] (i, j) original ids, i < j
     bm::DevBuf<uint64_t> d_fail_off;      // [n+1] failed tids per item (CSR)
     bm::DevBuf<uint32_t> d_fail_tid;      // [n_failed], sorted per item
+    // 3-of-4 sets (original item order): byte offsets, log2 r_i, own copy of pi_0..pi_3
+    bm::DevBuf<uint64_t> d_base;          // [n+1]
+    bm::DevBuf<uint32_t> d_rlog;          // [n]
+    bm::DevBuf<uint32_t> d_perm;          // [4 m]
 
     // timing of the most recent calls
     bm::PhaseEvents build_ev, pairs_ev;

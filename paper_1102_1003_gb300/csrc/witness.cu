@@ -1,0 +1,602 @@
+// d-of-(d+1) BatMaps and k-way supports (the generalisation that closes
+// Sec. V), and frequent itemsets of size 3 (the problem of Sec. I beyond
+// pairs, by the Apriori join-and-prune step over the frequent pairs).
+//
+// Layout (d = 3): the BatMap of item i has four tables of r_i byte slots,
+// interleaved in blocks of r_0 as Sec. III-A interleaves three (block size
+// 4 r_0); slot h_t(x) = 4 r_0 floor((pi_t(x) mod r_i) / r_0)
+// + (pi_t(x) mod r_0) + t r_0; width 4 r_i bytes = r_i words.  Every stored
+// element has copies in exactly three tables; each copy's byte holds the
+// fourth (missing) table in bits 7..6 and the code (pi_t(x) >> s) + 1 in bits
+// 5..0; 0x00 is empty and s is the smallest shift >= min_shift with
+// m <= 63 * 2^s.
+//
+// Witness rule: k <= 3 sets that all hold x miss at most three of the four
+// tables, so at least one table holds all k copies (pigeonhole); the slot of
+// table t counts iff the six code bits agree and are nonzero and t is the
+// smallest table that none of the k sets misses.  Exactly one table
+// satisfies this for every common element, and the rule reads only the k
+// bytes of the slot and t.
+//
+// Failed insertions (elements left with fewer than three copies) are deleted
+// and listed in F_i; a k-way support adds the common elements that failed in
+// at least one of the k sets, each once.
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "items.cuh"
+#include "scan.cuh"
+
+namespace bm {
+namespace wit {
+
+constexpr uint32_t TABLES = 4;  // d + 1
+constexpr uint32_t COPIES = 3;  // d
+constexpr uint32_t CODE_MASK = 0x3Fu;
+
+__host__ __device__ __forceinline__ uint64_t slot4(uint32_t t, uint32_t pi, uint32_t r, uint32_t shift) {
+    const uint32_t r0 = 1u << shift;
+    const uint32_t h = pi & (r - 1u);
+    return 4ull * r0 * (uint64_t)(h >> shift) + (h & (r0 - 1u)) + (uint64_t)t * r0;
+}
+
+__device__ __forceinline__ uint32_t code6(uint32_t pi, uint32_t shift) { return (pi >> shift) + 1u; }
+
+// ---- build ------------------------------------------------------------------
+
+// Parallel INSERT with three copies: copy c of every element starts in table
+// c; a copy is swapped into its slot and the evicted occupant continues in
+// the next table (0, 1, 2, 3, 0, ...).  Swapping with another copy of the
+// same element leaves the slot unchanged and the element moves on, so copies
+// of one element never share a table.  A chain longer than max_moves drops
+// the copy it holds (the element then fails).
+__global__ void k_place(ItemView v, const uint32_t *__restrict__ perm, uint32_t m, uint32_t shift,
+                        uint32_t max_moves, uint32_t *__restrict__ table) {
+    uint32_t item;
+    uint64_t e0, e1;
+    chunk_range(v, blockIdx.x / COPIES, &item, &e0, &e1);
+    const uint32_t copy = blockIdx.x % COPIES;
+    const uint64_t base = v.base[item];
+    const uint32_t r = 1u << v.rlog[item];
+    for (uint64_t e = e0 + threadIdx.x; e < e1; e += TPB) {
+        uint32_t x = v.tids[e];
+        if (x >= m) continue;  // rejected by validation; never index past perm
+        uint32_t t = copy;
+        for (uint32_t mv = 0; mv < max_moves; mv++) {
+            const uint32_t pi = __ldg(&perm[(uint64_t)t * m + x]);
+            const uint32_t old = atomicExch(&table[base + slot4(t, pi, r, shift)], x);
+            if (old == EMPTY) break;
+            x = old;
+            t = (t + 1u) & 3u;
+        }
+    }
+}
+
+struct Copies4 {
+    uint32_t pi[TABLES];
+    uint64_t pos[TABLES];
+    uint32_t has;  // bit t: a copy sits in table t
+};
+
+__device__ __forceinline__ Copies4 find_copies(uint32_t x, uint64_t base, uint32_t r, uint32_t shift,
+                                               const uint32_t *__restrict__ perm, uint32_t m,
+                                               const uint32_t *__restrict__ table) {
+    Copies4 c;
+    c.has = 0;
+#pragma unroll
+    for (uint32_t t = 0; t < TABLES; t++) {
+        c.pi[t] = __ldg(&perm[(uint64_t)t * m + x]);
+        c.pos[t] = base + slot4(t, c.pi[t], r, shift);
+        if (table[c.pos[t]] == x) c.has |= 1u << t;
+    }
+    return c;
+}
+
+// Bytes of every element stored three times; failures counted per block.
+__global__ void k_finalize(ItemView v, const uint32_t *__restrict__ perm, uint32_t m, uint32_t shift,
+                           const uint32_t *__restrict__ table, uint8_t *__restrict__ out,
+                           uint64_t *__restrict__ blocksums) {
+    __shared__ uint32_t s_fail;
+    if (threadIdx.x == 0) s_fail = 0;
+    __syncthreads();
+    uint32_t item;
+    uint64_t e0, e1;
+    chunk_range(v, blockIdx.x, &item, &e0, &e1);
+    const uint64_t base = v.base[item];
+    const uint32_t r = 1u << v.rlog[item];
+    uint32_t fails = 0;
+    for (uint64_t e = e0 + threadIdx.x; e < e1; e += TPB) {
+        const uint32_t x = v.tids[e];
+        if (x >= m) continue;
+        const Copies4 c = find_copies(x, base, r, shift, perm, m, table);
+        if (__popc(c.has) != (int)COPIES) {
+            fails++;
+            continue;
+        }
+        const uint32_t missing = __ffs(~c.has & 0xFu) - 1;
+#pragma unroll
+        for (uint32_t t = 0; t < TABLES; t++)
+            if (c.has & (1u << t)) out[c.pos[t]] = (uint8_t)((missing << 6) | code6(c.pi[t], shift));
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) fails += __shfl_xor_sync(0xffffffffu, fails, d);
+    if ((threadIdx.x & 31) == 0 && fails) atomicAdd(&s_fail, fails);
+    __syncthreads();
+    if (threadIdx.x == 0) blocksums[blockIdx.x] = s_fail;
+}
+
+// Failed insertions in (item, tid) order: block offsets come from the scan
+// of the finalize counts.
+__global__ void k_failures(ItemView v, const uint32_t *__restrict__ perm, uint32_t m, uint32_t shift,
+                           const uint32_t *__restrict__ table, const uint64_t *blocksums, uint32_t *f_item,
+                           uint32_t *f_tid) {
+    uint32_t item;
+    uint64_t e0, e1;
+    chunk_range(v, blockIdx.x, &item, &e0, &e1);
+    uint64_t running = blocksums[blockIdx.x];
+    if (blocksums[blockIdx.x + 1] == running) return;  // no failure in this block
+    const uint64_t base = v.base[item];
+    const uint32_t r = 1u << v.rlog[item];
+    for (int j = 0; j < PER_THREAD; j++) {
+        const uint64_t e = e0 + (uint64_t)j * TPB + threadIdx.x;
+        bool fail = false;
+        uint32_t x = 0;
+        if (e < e1) {
+            x = v.tids[e];
+            fail = x < m && __popc(find_copies(x, base, r, shift, perm, m, table).has) != (int)COPIES;
+        }
+        uint64_t tot;
+        const uint64_t rank = block_exclusive_scan(fail ? 1 : 0, &tot);
+        if (fail) {
+            f_item[running + rank] = item;
+            f_tid[running + rank] = x;
+        }
+        running += tot;
+    }
+}
+
+static uint32_t shift_bits63(uint32_t m, uint32_t min_shift) {
+    uint32_t s = min_shift;
+    while ((uint64_t)m > 63ull << s) s++;
+    return s;
+}
+
+}  // namespace wit
+
+void build_witness_set(batmap_set *S, const uint64_t *d_offsets, const uint32_t *d_tids,
+                       const uint32_t *d_perm) {
+    using namespace wit;
+    std::lock_guard<std::mutex> scratch_lock(g_scratch_mu);
+    const uint32_t m = S->m, n = S->n;
+    cudaStream_t st = S->stream;
+    const batmap_params &P = S->params;
+    PhaseEvents &E = S->build_ev;
+    E.create();
+    E.record(0, st);
+
+    std::vector<uint64_t> off(n + 1, 0);
+    if (n) {
+        BM_REQUIRE(d_offsets != nullptr, BATMAP_ERR_ARG, "d_offsets is NULL");
+        BM_CUDA(cudaMemcpyAsync(off.data(), d_offsets, (n + 1) * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+        BM_CUDA(cudaStreamSynchronize(st));
+    }
+    BM_REQUIRE(off[0] == 0, BATMAP_ERR_ARG, "offsets[0] must be 0");
+    for (uint32_t i = 0; i < n; i++)
+        BM_REQUIRE(off[i + 1] >= off[i], BATMAP_ERR_ARG, "offsets must be non-decreasing");
+    const uint64_t T = off[n];
+    S->n_elements = T;
+    BM_REQUIRE(T == 0 || d_tids != nullptr, BATMAP_ERR_ARG, "d_tids is NULL");
+    BM_REQUIRE(d_perm != nullptr, BATMAP_ERR_ARG, "d_perm is NULL");
+
+    // ---- sizes: four tables of r_i slots; items keep their original order ----
+    S->shift = shift_bits63(m, P.min_shift);
+    S->r0 = 1u << S->shift;
+    std::vector<uint32_t> rlog(n);
+    std::vector<uint64_t> base(n + 1, 0);
+    S->range.resize(n);
+    for (uint32_t i = 0; i < n; i++) {
+        rlog[i] = log2_range(off[i + 1] - off[i], P.load_num, P.load_den, S->shift);
+        BM_REQUIRE(rlog[i] <= 30, BATMAP_ERR_ARG, "hash range exceeds 2^30");
+        S->range[i] = 1u << rlog[i];
+        base[i + 1] = base[i] + (4ull << rlog[i]);
+    }
+    S->bytes = base[n];
+    S->order.resize(n);
+    S->rank.resize(n);
+    S->byte_off.assign(base.begin(), base.begin() + n);
+    for (uint32_t i = 0; i < n; i++) S->order[i] = S->rank[i] = i;
+    S->word_pairs = 0.0;
+
+    S->d_bm.alloc(S->bytes);
+    S->d_base.alloc(n + 1);
+    S->d_rlog.alloc(n);
+    S->d_perm.alloc((uint64_t)TABLES * m);
+    if (n) {
+        BM_CUDA(cudaMemcpyAsync(S->d_base.p, base.data(), (n + 1) * 8ull, cudaMemcpyHostToDevice, st));
+        BM_CUDA(cudaMemcpyAsync(S->d_rlog.p, rlog.data(), n * 4ull, cudaMemcpyHostToDevice, st));
+    }
+    BM_CUDA(cudaMemcpyAsync(S->d_perm.p, d_perm, (uint64_t)TABLES * m * 4, cudaMemcpyDeviceToDevice, st));
+    if (S->bytes) BM_CUDA(cudaMemsetAsync(S->d_bm.p, 0, S->bytes, st));
+    S->d_fail_off.alloc(n + 1);
+
+    std::vector<uint32_t> ch_item;
+    std::vector<uint64_t> ch_start;
+    for (uint32_t i = 0; i < n; i++)
+        for (uint64_t s0 = off[i]; s0 < off[i + 1]; s0 += CHUNK) {
+            ch_item.push_back(i);
+            ch_start.push_back(s0);
+        }
+    const uint32_t nch = (uint32_t)ch_item.size();
+    DevBuf<uint32_t> d_ch_item(nch);
+    DevBuf<uint64_t> d_ch_start(nch);
+    if (nch) {
+        BM_CUDA(cudaMemcpyAsync(d_ch_item.p, ch_item.data(), nch * 4ull, cudaMemcpyHostToDevice, st));
+        BM_CUDA(cudaMemcpyAsync(d_ch_start.p, ch_start.data(), nch * 8ull, cudaMemcpyHostToDevice, st));
+    }
+    ItemView v{d_offsets, d_tids, S->d_base.p, S->d_rlog.p, d_ch_item.p, d_ch_start.p};
+
+    if (P.validate) {
+        DevBuf<int> d_err(1);
+        DevBuf<uint32_t> d_bits((uint64_t)TABLES * ((m + 31) / 32));
+        BM_CUDA(cudaMemsetAsync(d_err.p, 0, sizeof(int), st));
+        BM_CUDA(cudaMemsetAsync(d_bits.p, 0, d_bits.bytes(), st));
+        if (nch) {
+            k_validate_tids<<<nch, TPB, 0, st>>>(v, m, d_err.p);
+            BM_CHECK_LAUNCH();
+        }
+        k_validate_perm<<<grid_for((uint64_t)TABLES * m), 256, 0, st>>>(d_perm, m, TABLES, d_bits.p, d_err.p);
+        BM_CHECK_LAUNCH();
+        int err = 0;
+        BM_CUDA(cudaMemcpyAsync(&err, d_err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        BM_CUDA(cudaStreamSynchronize(st));
+        BM_REQUIRE(err != 1, BATMAP_ERR_ARG, "tids must be strictly increasing per item and < m");
+        BM_REQUIRE(err != 2, BATMAP_ERR_ARG, "each permutation row must be a bijection of [0, m)");
+    }
+
+    S->n_failed = 0;
+    if (nch) {
+        DevBuf<uint32_t> &table = scratch_table(S->bytes);
+        BM_CUDA(cudaMemsetAsync(table.p, 0xFF, S->bytes * sizeof(uint32_t), st));
+        const uint32_t max_moves = TABLES * std::max<uint32_t>(P.max_loop, 1u);
+        E.record(2, st);
+        k_place<<<COPIES * nch, TPB, 0, st>>>(v, S->d_perm.p, m, S->shift, max_moves, table.p);
+        BM_CHECK_LAUNCH();
+        E.record(3, st);
+        DevBuf<uint64_t> bs(nch + 1), d_tot(1);
+        k_finalize<<<nch, TPB, 0, st>>>(v, S->d_perm.p, m, S->shift, table.p, S->d_bm.p, bs.p);
+        BM_CHECK_LAUNCH();
+        k_scan_single_block<<<1, SCAN_TPB, 0, st>>>(bs.p, nch, d_tot.p, 1);
+        BM_CHECK_LAUNCH();
+        uint64_t nfail = 0;
+        BM_CUDA(cudaMemcpyAsync(&nfail, d_tot.p, 8, cudaMemcpyDeviceToHost, st));
+        BM_CUDA(cudaStreamSynchronize(st));
+        S->n_failed = nfail;
+        DevBuf<uint32_t> f_item(nfail);
+        S->d_fail_tid.alloc(nfail);
+        if (nfail) {
+            k_failures<<<nch, TPB, 0, st>>>(v, S->d_perm.p, m, S->shift, table.p, bs.p, f_item.p,
+                                            S->d_fail_tid.p);
+            BM_CHECK_LAUNCH();
+        }
+        k_fail_offsets<<<(n + 1 + 255) / 256, 256, 0, st>>>(f_item.p, nfail, n, S->d_fail_off.p);
+        BM_CHECK_LAUNCH();
+        E.record(4, st);
+    } else {
+        BM_CUDA(cudaMemsetAsync(S->d_fail_off.p, 0, (n + 1) * sizeof(uint64_t), st));
+        E.record(2, st);
+        E.record(3, st);
+        E.record(4, st);
+    }
+    E.record(1, st);
+    BM_CUDA(cudaStreamSynchronize(st));
+    S->timing.build_ms = E.ms(0, 1);
+    S->timing.place_ms = E.ms(2, 3);
+    S->timing.finalize_ms = E.ms(3, 4);
+}
+
+namespace wit {
+
+// ---- k-way supports ------------------------------------------------------------
+
+struct View {
+    const uint32_t *bm;     // BatMap bytes as 32-bit words
+    const uint64_t *base;   // [n+1] byte offset of item i
+    const uint32_t *rlog;   // [n] log2 r_i (r_i words per BatMap)
+    const uint32_t *perm;   // [4 m]
+    const uint64_t *f_off;  // [n+1] failed insertions (CSR, sorted tids)
+    const uint32_t *f_tid;
+    uint32_t m, n, shift;
+};
+
+// Counted slots among the four lanes of one word of each of K BatMaps, all in
+// table t.  Bit 6 of lane q of (v & 0x3F..) + 0x3F.. is set iff the lane's
+// six low bits are nonzero (0x3F + 0x3F < 0x80: no carry leaves a lane).
+template <int K>
+__device__ __forceinline__ uint32_t witness_word(const uint32_t (&x)[K], uint32_t t) {
+    constexpr uint32_t C6 = 0x3F3F3F3Fu, B6 = 0x40404040u;
+    uint32_t diff = 0;
+#pragma unroll
+    for (int j = 1; j < K; j++) diff |= x[0] ^ x[j];
+    const uint32_t ne = ((diff & C6) + C6) & B6;   // codes differ somewhere
+    const uint32_t nz = ((x[0] & C6) + C6) & B6;   // slot not empty
+    uint32_t ok = nz & ~ne;
+    if (t == 0) return __popc(ok);
+    // e_u (bit 6 of each lane): some set misses table u
+    uint32_t e0 = 0, e1 = 0, e2 = 0;
+#pragma unroll
+    for (int j = 0; j < K; j++) {
+        const uint32_t hi = (x[j] >> 1) & B6, lo = x[j] & B6;
+        e0 |= ~(hi | lo) & B6;
+        e1 |= ~hi & lo;
+        e2 |= hi & ~lo;
+    }
+    ok &= e0;
+    if (t >= 2) ok &= e1;
+    if (t >= 3) ok &= e2;
+    return __popc(ok);
+}
+
+// x is stored in item's BatMap: a copy sits in table 0 or table 1 (three of
+// four tables hold one), recognised by its code at h_t(x).
+__device__ __forceinline__ bool stored_in(const View &V, uint32_t item, uint32_t x) {
+    const uint32_t r = 1u << V.rlog[item];
+    const uint8_t *b = reinterpret_cast<const uint8_t *>(V.bm) + V.base[item];
+#pragma unroll
+    for (uint32_t t = 0; t < 2; t++) {
+        const uint32_t pi = __ldg(&V.perm[(uint64_t)t * V.m + x]);
+        if ((b[slot4(t, pi, r, V.shift)] & CODE_MASK) == code6(pi, V.shift)) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ bool failed_in(const View &V, uint32_t item, uint32_t x) {
+    uint64_t lo = V.f_off[item], hi = V.f_off[item + 1];
+    while (lo < hi) {
+        const uint64_t mid = (lo + hi) >> 1;
+        const uint32_t y = V.f_tid[mid];
+        if (y == x) return true;
+        if (y < x) lo = mid + 1; else hi = mid;
+    }
+    return false;
+}
+
+// One warp per query of K item ids.  Lane l reads word w = w0 + l of every
+// BatMap, the narrower ones cyclically (w mod r_i); 32 consecutive words lie
+// in one table because a table block is r_0 >= 128 bytes.
+template <int K>
+__global__ void __launch_bounds__(256) k_witness(View V, const uint32_t *__restrict__ items, uint64_t nq,
+                                                 uint32_t *__restrict__ out) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x / 32);
+    for (uint64_t q = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) / 32; q < nq; q += nwarps) {
+        uint32_t it[K], mask[K];
+        uint64_t wb[K];
+        uint32_t rmax = 0;
+#pragma unroll
+        for (int j = 0; j < K; j++) {
+            it[j] = __ldg(&items[q * K + j]);
+            const uint32_t r = 1u << V.rlog[it[j]];
+            mask[j] = r - 1u;
+            wb[j] = V.base[it[j]] >> 2;
+            rmax = r > rmax ? r : rmax;
+        }
+        const uint32_t tshift = V.shift - 2;  // words per table block = r_0 / 4
+        uint32_t cnt = 0;
+        for (uint32_t w = lane; w < rmax; w += 32) {
+            uint32_t x[K];
+#pragma unroll
+            for (int j = 0; j < K; j++) x[j] = __ldg(&V.bm[wb[j] + (w & mask[j])]);
+            cnt += witness_word<K>(x, (w >> tshift) & 3u);
+        }
+        // failed common elements: x from F of set j counts unless an earlier
+        // set i < j also failed it (then it is counted from set i's list)
+#pragma unroll
+        for (int j = 0; j < K; j++) {
+            const uint64_t f1 = V.f_off[it[j] + 1];
+            for (uint64_t f = V.f_off[it[j]] + lane; f < f1; f += 32) {
+                const uint32_t x = V.f_tid[f];
+                bool all = true;
+#pragma unroll
+                for (int i = 0; i < K; i++) {
+                    if (i == j || !all) continue;
+                    const bool fi = failed_in(V, it[i], x);
+                    if (i < j && fi) all = false;
+                    else all = fi || stored_in(V, it[i], x);
+                }
+                cnt += all ? 1u : 0u;
+            }
+        }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, d);
+        if (lane == 0) out[q] = cnt;
+    }
+}
+
+__global__ void k_check_ids(const uint32_t *ids, uint64_t count, uint32_t n, int *err) {
+    for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < count;
+         k += (uint64_t)gridDim.x * blockDim.x)
+        if (ids[k] >= n) atomicExch(err, 1);
+}
+
+// ---- Apriori level 3 ------------------------------------------------------------
+
+// Frequent pairs (i, j, support), i < j, lexicographic: err <- 1 unless the
+// list is strictly increasing with ids < n.  row_off[i] = first pair of row i.
+__global__ void k_check_pairs(const uint32_t *pairs, uint64_t np, uint32_t n, int *err) {
+    for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < np;
+         p += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t a = pairs[3 * p], b = pairs[3 * p + 1];
+        bool bad = !(a < b) || b >= n;
+        if (p + 1 < np) {
+            const uint32_t a2 = pairs[3 * p + 3], b2 = pairs[3 * p + 4];
+            bad |= !(a < a2 || (a == a2 && b < b2));
+        }
+        if (bad) atomicExch(err, 1);
+    }
+}
+
+__global__ void k_pair_rows(const uint32_t *pairs, uint64_t np, uint32_t n, uint64_t *row_off) {
+    const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (i > n) return;
+    uint64_t lo = 0, hi = np;
+    while (lo < hi) {
+        const uint64_t mid = (lo + hi) >> 1;
+        if (pairs[3 * mid] < i) lo = mid + 1; else hi = mid;
+    }
+    row_off[i] = lo;
+}
+
+// For the frequent pair p = (a, b): every c > b with (a, c) and (b, c)
+// frequent -- the merge of the rest of row a after p with row b (both
+// ascending).  COUNT writes the number into cnt[p]; otherwise the triples
+// are written from offset cnt[p] (the exclusive scan of the counts).
+template <bool WRITE>
+__global__ void k_candidates(const uint32_t *__restrict__ pairs, uint64_t np, const uint64_t *__restrict__ row_off,
+                             uint64_t *cnt, uint32_t *__restrict__ out) {
+    for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < np;
+         p += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t a = pairs[3 * p], b = pairs[3 * p + 1];
+        uint64_t u = p + 1, ue = row_off[a + 1], v = row_off[b], ve = row_off[b + 1];
+        uint64_t k = WRITE ? cnt[p] : 0;
+        while (u < ue && v < ve) {
+            const uint32_t cu = pairs[3 * u + 1], cv = pairs[3 * v + 1];
+            if (cu < cv) {
+                u++;
+            } else if (cv < cu) {
+                v++;
+            } else {
+                if (WRITE) {
+                    out[3 * k] = a;
+                    out[3 * k + 1] = b;
+                    out[3 * k + 2] = cu;
+                }
+                k++;
+                u++;
+                v++;
+            }
+        }
+        if (!WRITE) cnt[p] = k;
+    }
+}
+
+// Ordered compaction of the candidates with support >= s into (a, b, c, support).
+constexpr int TH_PER = 8;
+template <bool WRITE>
+__global__ void k_triple_threshold(const uint32_t *__restrict__ cand, const uint32_t *__restrict__ sup, uint64_t nc,
+                                   uint32_t s, uint64_t *blocksums, uint32_t *__restrict__ out, uint64_t cap) {
+    const uint64_t b0 = (uint64_t)blockIdx.x * SCAN_TPB * TH_PER;
+    uint64_t running = WRITE ? blocksums[blockIdx.x] : 0;
+    for (int j = 0; j < TH_PER; j++) {
+        const uint64_t c = b0 + (uint64_t)j * SCAN_TPB + threadIdx.x;
+        const bool keep = c < nc && sup[c] >= s;
+        uint64_t tot;
+        const uint64_t rank = block_exclusive_scan(keep ? 1 : 0, &tot);
+        if (WRITE && keep && running + rank < cap) {
+            const uint64_t o = 4 * (running + rank);
+            out[o] = cand[3 * c];
+            out[o + 1] = cand[3 * c + 1];
+            out[o + 2] = cand[3 * c + 2];
+            out[o + 3] = sup[c];
+        }
+        running += tot;
+    }
+    if (!WRITE && threadIdx.x == 0) blocksums[blockIdx.x] = running;
+}
+
+}  // namespace wit
+
+// Supports of n_q queries of k item ids each (k in 1..3) on a 3-of-4 set.
+void witness_support(batmap_set *S, uint32_t k, uint64_t nq, const uint32_t *d_items, uint32_t *d_support,
+                     cudaStream_t st) {
+    using namespace wit;
+    BM_REQUIRE(S && S->d == 3, BATMAP_ERR_ARG, "itemset supports need a set built with d = 3");
+    BM_REQUIRE(k >= 1 && k <= 3, BATMAP_ERR_ARG, "k must be 1, 2 or 3");
+    if (nq == 0) return;
+    BM_REQUIRE(d_items && d_support, BATMAP_ERR_ARG, "NULL argument");
+    {
+        DevBuf<int> err(1);
+        BM_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
+        k_check_ids<<<grid_for(nq * k), 256, 0, st>>>(d_items, nq * k, S->n, err.p);
+        BM_CHECK_LAUNCH();
+        int h = 0;
+        BM_CUDA(cudaMemcpyAsync(&h, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        BM_CUDA(cudaStreamSynchronize(st));
+        BM_REQUIRE(h == 0, BATMAP_ERR_ARG, "item id >= n in a query");
+    }
+    const View V{reinterpret_cast<const uint32_t *>(S->d_bm.p), S->d_base.p, S->d_rlog.p, S->d_perm.p,
+                 S->d_fail_off.p, S->d_fail_tid.p, S->m, S->n, S->shift};
+    const unsigned grid = (unsigned)std::min<uint64_t>((nq + 7) / 8, 152ull * 64);
+    if (k == 1) k_witness<1><<<grid, 256, 0, st>>>(V, d_items, nq, d_support);
+    if (k == 2) k_witness<2><<<grid, 256, 0, st>>>(V, d_items, nq, d_support);
+    if (k == 3) k_witness<3><<<grid, 256, 0, st>>>(V, d_items, nq, d_support);
+    BM_CHECK_LAUNCH();
+}
+
+// Frequent itemsets of size 3 from the frequent pairs (Apriori join and
+// prune), supports by the witness rule, compaction in lexicographic order.
+void frequent_triples(batmap_set *S, uint32_t s, const uint32_t *d_pairs, uint64_t np, uint32_t *d_out,
+                      uint64_t cap, uint64_t *n_out, uint64_t *n_cand, cudaStream_t st) {
+    using namespace wit;
+    BM_REQUIRE(S && S->d == 3, BATMAP_ERR_ARG, "frequent_triples needs a set built with d = 3");
+    BM_REQUIRE(n_out, BATMAP_ERR_ARG, "n_out is NULL");
+    BM_REQUIRE(np == 0 || d_pairs, BATMAP_ERR_ARG, "d_pairs is NULL");
+    BM_REQUIRE(cap == 0 || d_out, BATMAP_ERR_ARG, "d_out is NULL with cap > 0");
+    PhaseEvents &E = S->pairs_ev;
+    E.create();
+    E.record(0, st);
+    const uint32_t n = S->n;
+    uint64_t nc = 0;
+    DevBuf<uint32_t> cand, sup;
+    if (np) {
+        DevBuf<int> err(1);
+        BM_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
+        k_check_pairs<<<grid_for(np), 256, 0, st>>>(d_pairs, np, n, err.p);
+        BM_CHECK_LAUNCH();
+        DevBuf<uint64_t> row_off(n + 1), cnt(np + 1), tot(1);
+        k_pair_rows<<<grid_for(n + 1), 256, 0, st>>>(d_pairs, np, n, row_off.p);
+        BM_CHECK_LAUNCH();
+        int h = 0;
+        BM_CUDA(cudaMemcpyAsync(&h, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        BM_CUDA(cudaStreamSynchronize(st));
+        BM_REQUIRE(h == 0, BATMAP_ERR_ARG, "pairs must be (i, j, support) with i < j < n, lexicographic");
+        k_candidates<false><<<grid_for(np), 256, 0, st>>>(d_pairs, np, row_off.p, cnt.p, nullptr);
+        BM_CHECK_LAUNCH();
+        scan_exclusive(cnt.p, np, tot.p, st);
+        BM_CUDA(cudaMemcpyAsync(&nc, tot.p, 8, cudaMemcpyDeviceToHost, st));
+        BM_CUDA(cudaStreamSynchronize(st));
+        cand.alloc(3 * nc);
+        sup.alloc(nc);
+        if (nc) {
+            k_candidates<true><<<grid_for(np), 256, 0, st>>>(d_pairs, np, row_off.p, cnt.p, cand.p);
+            BM_CHECK_LAUNCH();
+        }
+    }
+    if (n_cand) *n_cand = nc;
+    E.record(1, st);
+    if (nc) witness_support(S, 3, nc, cand.p, sup.p, st);
+    E.record(2, st);
+    uint64_t total = 0;
+    if (nc) {
+        const uint64_t per_block = (uint64_t)SCAN_TPB * TH_PER;
+        const uint64_t nb = (nc + per_block - 1) / per_block;
+        DevBuf<uint64_t> bs(nb + 1), tot(1);
+        k_triple_threshold<false><<<(unsigned)nb, SCAN_TPB, 0, st>>>(cand.p, sup.p, nc, s, bs.p, nullptr, 0);
+        BM_CHECK_LAUNCH();
+        k_scan_single_block<<<1, SCAN_TPB, 0, st>>>(bs.p, nb, tot.p, 1);
+        BM_CHECK_LAUNCH();
+        k_triple_threshold<true><<<(unsigned)nb, SCAN_TPB, 0, st>>>(cand.p, sup.p, nc, s, bs.p, d_out, cap);
+        BM_CHECK_LAUNCH();
+        BM_CUDA(cudaMemcpyAsync(&total, tot.p, 8, cudaMemcpyDeviceToHost, st));
+    }
+    E.record(3, st);
+    BM_CUDA(cudaStreamSynchronize(st));
+    S->timing.compare_ms = E.ms(1, 2);
+    S->timing.compact_ms = E.ms(0, 1) + E.ms(2, 3);
+    S->timing.pairs_ms = E.ms(0, 3);
+    *n_out = total;
+    if (total > cap)
+        throw Error{BATMAP_ERR_CAPACITY, "d_out too small: " + std::to_string(total) + " triples qualify"};
+}
+
+}  // namespace bm
