@@ -32,7 +32,7 @@ __all__ = [
     "Instance", "bernoulli_item", "bernoulli_tidlists", "zipf_probabilities",
     "zipf_tidlists", "permutations", "config_instance", "batch_specs",
     "pool_sizes", "pool_tidlists", "from_lists", "transactions_to_tidlists",
-    "CONFIGS", "concat", "cross_instance",
+    "CONFIGS", "concat", "cross_instance", "triples_instance",
 ]
 
 
@@ -191,6 +191,16 @@ def cross_instance(m: int = CROSS["m"], n_a: int = CROSS["n_a"], n_b: int = CROS
     a = zipf_tidlists(m, n_a, density_a, seed)
     b = bernoulli_tidlists(m, n_b, p_b, seed + 1)
     return concat(a, b, name="cross"), n_a
+
+
+TRIPLES = dict(m=100_000, n=1_000, density=0.02, s=100, seed=71)
+
+
+def triples_instance() -> Instance:
+    """Frequent-itemset workload beyond pairs: m = 100,000 transactions, n = 1,000
+    items with Zipf(1) inclusion probabilities at mean density 2%, s = 100 (0.1%)."""
+    c = TRIPLES
+    return zipf_tidlists(c["m"], c["n"], c["density"], c["seed"], 1.0, c["s"], "triples")
 
 
 def batch_specs(k: int = 64, seed0: int = 1000, m_range=(1e4, 1e6), n_range=(100, 4000),

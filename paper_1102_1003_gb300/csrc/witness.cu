@@ -361,6 +361,31 @@ __device__ __forceinline__ bool failed_in(const View &V, uint32_t item, uint32_t
     return false;
 }
 
+// The lane's share of the failed common elements of the K sets: x from F of
+// set j counts unless an earlier set i < j also failed it (then it is
+// counted from set i's list).
+template <int K>
+__device__ __forceinline__ uint32_t failed_common(const View &V, const uint32_t (&it)[K], uint32_t lane) {
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int j = 0; j < K; j++) {
+        const uint64_t f1 = V.f_off[it[j] + 1];
+        for (uint64_t f = V.f_off[it[j]] + lane; f < f1; f += 32) {
+            const uint32_t x = V.f_tid[f];
+            bool all = true;
+#pragma unroll
+            for (int i = 0; i < K; i++) {
+                if (i == j || !all) continue;
+                const bool fi = failed_in(V, it[i], x);
+                if (i < j && fi) all = false;
+                else all = fi || stored_in(V, it[i], x);
+            }
+            cnt += all ? 1u : 0u;
+        }
+    }
+    return cnt;
+}
+
 // One warp per query of K item ids.  Lane l reads word w = w0 + l of every
 // BatMap, the narrower ones cyclically (w mod r_i); 32 consecutive words lie
 // in one table because a table block is r_0 >= 128 bytes.
@@ -389,24 +414,7 @@ __global__ void __launch_bounds__(256) k_witness(View V, const uint32_t *__restr
             for (int j = 0; j < K; j++) x[j] = __ldg(&V.bm[wb[j] + (w & mask[j])]);
             cnt += witness_word<K>(x, (w >> tshift) & 3u);
         }
-        // failed common elements: x from F of set j counts unless an earlier
-        // set i < j also failed it (then it is counted from set i's list)
-#pragma unroll
-        for (int j = 0; j < K; j++) {
-            const uint64_t f1 = V.f_off[it[j] + 1];
-            for (uint64_t f = V.f_off[it[j]] + lane; f < f1; f += 32) {
-                const uint32_t x = V.f_tid[f];
-                bool all = true;
-#pragma unroll
-                for (int i = 0; i < K; i++) {
-                    if (i == j || !all) continue;
-                    const bool fi = failed_in(V, it[i], x);
-                    if (i < j && fi) all = false;
-                    else all = fi || stored_in(V, it[i], x);
-                }
-                cnt += all ? 1u : 0u;
-            }
-        }
+        cnt += failed_common<K>(V, it, lane);
 #pragma unroll
         for (int d = 16; d > 0; d >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, d);
         if (lane == 0) out[q] = cnt;
@@ -417,6 +425,118 @@ __global__ void k_check_ids(const uint32_t *ids, uint64_t count, uint32_t n, int
     for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < count;
          k += (uint64_t)gridDim.x * blockDim.x)
         if (ids[k] >= n) atomicExch(err, 1);
+}
+
+// ---- grouped triple supports ------------------------------------------------------
+//
+// The candidates of the frequent pair p = (a, b) are contiguous
+// (cand_off[p] .. cand_off[p+1]).  A work unit is up to GROUP of them: the
+// warp reads a's and b's words once per step and every c of the unit against
+// them.  Lanes read 16-byte chunks; a table block is r_0 >= 128 bytes, so the
+// four words of a chunk share one table (lanes may differ: the witness
+// requirement is selected per lane).
+constexpr uint32_t GROUP = 8;
+
+__global__ void k_unit_counts(const uint64_t *cand_off, uint64_t np, uint64_t *ucnt) {
+    for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < np;
+         p += (uint64_t)gridDim.x * blockDim.x)
+        ucnt[p] = (cand_off[p + 1] - cand_off[p] + GROUP - 1) / GROUP;
+}
+
+__global__ void k_unit_fill(const uint64_t *cand_off, const uint64_t *uoff, uint64_t np, uint2 *units) {
+    for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < np;
+         p += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t nu = uoff[p + 1] - uoff[p];
+        for (uint64_t q = 0; q < nu; q++) units[uoff[p] + q] = make_uint2((uint32_t)p, (uint32_t)(q * GROUP));
+    }
+}
+
+__global__ void __launch_bounds__(256) k_witness_group(View V, const uint32_t *__restrict__ pairs,
+                                                       const uint64_t *__restrict__ cand_off,
+                                                       const uint32_t *__restrict__ cand,
+                                                       const uint2 *__restrict__ units, uint64_t nu,
+                                                       uint32_t *__restrict__ sup) {
+    constexpr uint32_t C6 = 0x3F3F3F3Fu, B6 = 0x40404040u;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint4 *bm4 = reinterpret_cast<const uint4 *>(V.bm);
+    const uint32_t tq = V.shift - 4;  // 16-byte chunks per table block = r_0 / 16 = 2^(s-4)
+    const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x / 32);
+    for (uint64_t uid = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) / 32; uid < nu; uid += nwarps) {
+        const uint2 u = units[uid];
+        const uint64_t c0 = cand_off[u.x] + u.y;
+        const uint64_t left = cand_off[u.x + 1] - c0;
+        const uint32_t gn = left < GROUP ? (uint32_t)left : GROUP;
+        const uint32_t a = pairs[3ull * u.x], b = pairs[3ull * u.x + 1];
+        const uint32_t ra = 1u << V.rlog[a], rb = 1u << V.rlog[b];
+        const uint64_t ca = V.base[a] >> 4, cb = V.base[b] >> 4;
+        const uint32_t ma = ra / 4 - 1, mb = rb / 4 - 1;
+        uint64_t cc[GROUP];
+        uint32_t mc[GROUP], lim[GROUP], cnt[GROUP];
+        uint32_t qmax = 0;
+#pragma unroll
+        for (uint32_t j = 0; j < GROUP; j++) {
+            cnt[j] = 0;
+            if (j < gn) {
+                const uint32_t c = cand[3 * (c0 + j) + 2];
+                const uint32_t rc = 1u << V.rlog[c];
+                cc[j] = V.base[c] >> 4;
+                mc[j] = rc / 4 - 1;
+                lim[j] = max(max(ra, rb), rc) / 4;  // chunks this triple runs over
+            } else {
+                cc[j] = 0;
+                mc[j] = 0;
+                lim[j] = 0;
+            }
+            qmax = max(qmax, lim[j]);
+        }
+        for (uint32_t q = lane; q < qmax; q += 32) {
+            const uint32_t t = (q >> tq) & 3u;
+            const uint32_t f0 = t >= 1 ? 0u : B6, f1 = t >= 2 ? 0u : B6, f2 = t >= 3 ? 0u : B6;
+            const uint4 A = __ldg(&bm4[ca + (q & ma)]);
+            const uint4 Bv = __ldg(&bm4[cb + (q & mb)]);
+            // all of the unit's column chunks are requested before any is used
+            uint4 Cs[GROUP];
+#pragma unroll
+            for (uint32_t j = 0; j < GROUP; j++)
+                Cs[j] = q < lim[j] ? __ldg(&bm4[cc[j] + (q & mc[j])]) : make_uint4(0, 0, 0, 0);
+            const uint32_t xa[4] = {A.x, A.y, A.z, A.w}, xb[4] = {Bv.x, Bv.y, Bv.z, Bv.w};
+            uint32_t dab[4], nza[4], e0[4], e1[4], e2[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                dab[k] = xa[k] ^ xb[k];
+                nza[k] = ((xa[k] & C6) + C6) & B6;
+                const uint32_t ha = (xa[k] >> 1) & B6, la = xa[k] & B6;
+                const uint32_t hb = (xb[k] >> 1) & B6, lb = xb[k] & B6;
+                e0[k] = (~(ha | la) | ~(hb | lb)) & B6;
+                e1[k] = (~ha & la) | (~hb & lb);
+                e2[k] = (ha & ~la) | (hb & ~lb);
+            }
+#pragma unroll
+            for (uint32_t j = 0; j < GROUP; j++) {
+                if (q >= lim[j]) continue;  // also skips the unit's unused slots (lim = 0)
+                const uint32_t xc[4] = {Cs[j].x, Cs[j].y, Cs[j].z, Cs[j].w};
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const uint32_t hc = (xc[k] >> 1) & B6, lc = xc[k] & B6;
+                    const uint32_t diff = dab[k] | (xa[k] ^ xc[k]);
+                    const uint32_t ne = ((diff & C6) + C6) & B6;
+                    const uint32_t E0 = e0[k] | (~(hc | lc) & B6) | f0;
+                    const uint32_t E1 = e1[k] | (~hc & lc) | f1;
+                    const uint32_t E2 = e2[k] | (hc & ~lc) | f2;
+                    cnt[j] += __popc(nza[k] & ~ne & E0 & E1 & E2);
+                }
+            }
+        }
+#pragma unroll
+        for (uint32_t j = 0; j < GROUP; j++) {
+            if (j >= gn) break;
+            const uint32_t it[3] = {a, b, cand[3 * (c0 + j) + 2]};
+            uint32_t v = cnt[j] + failed_common<3>(V, it, lane);
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+            if (lane == 0) sup[c0 + j] = v;
+        }
+    }
 }
 
 // ---- Apriori level 3 ------------------------------------------------------------
@@ -546,14 +666,17 @@ void frequent_triples(batmap_set *S, uint32_t s, const uint32_t *d_pairs, uint64
     E.create();
     E.record(0, st);
     const uint32_t n = S->n;
-    uint64_t nc = 0;
+    uint64_t nc = 0, n_units = 0;
     DevBuf<uint32_t> cand, sup;
+    DevBuf<uint2> units;
+    DevBuf<uint64_t> cnt;  // candidate offsets per frequent pair, [np + 1]
     if (np) {
         DevBuf<int> err(1);
         BM_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
         k_check_pairs<<<grid_for(np), 256, 0, st>>>(d_pairs, np, n, err.p);
         BM_CHECK_LAUNCH();
-        DevBuf<uint64_t> row_off(n + 1), cnt(np + 1), tot(1);
+        DevBuf<uint64_t> row_off(n + 1), tot(1);
+        cnt.alloc(np + 1);
         k_pair_rows<<<grid_for(n + 1), 256, 0, st>>>(d_pairs, np, n, row_off.p);
         BM_CHECK_LAUNCH();
         int h = 0;
@@ -562,7 +685,8 @@ void frequent_triples(batmap_set *S, uint32_t s, const uint32_t *d_pairs, uint64
         BM_REQUIRE(h == 0, BATMAP_ERR_ARG, "pairs must be (i, j, support) with i < j < n, lexicographic");
         k_candidates<false><<<grid_for(np), 256, 0, st>>>(d_pairs, np, row_off.p, cnt.p, nullptr);
         BM_CHECK_LAUNCH();
-        scan_exclusive(cnt.p, np, tot.p, st);
+        k_scan_single_block<<<1, SCAN_TPB, 0, st>>>(cnt.p, np, tot.p, 1);  // cnt[np] = total
+        BM_CHECK_LAUNCH();
         BM_CUDA(cudaMemcpyAsync(&nc, tot.p, 8, cudaMemcpyDeviceToHost, st));
         BM_CUDA(cudaStreamSynchronize(st));
         cand.alloc(3 * nc);
@@ -570,11 +694,30 @@ void frequent_triples(batmap_set *S, uint32_t s, const uint32_t *d_pairs, uint64
         if (nc) {
             k_candidates<true><<<grid_for(np), 256, 0, st>>>(d_pairs, np, row_off.p, cnt.p, cand.p);
             BM_CHECK_LAUNCH();
+            // work units of up to GROUP candidates sharing their frequent pair
+            DevBuf<uint64_t> uoff(np + 1), utot(1);
+            k_unit_counts<<<grid_for(np), 256, 0, st>>>(cnt.p, np, uoff.p);
+            BM_CHECK_LAUNCH();
+            k_scan_single_block<<<1, SCAN_TPB, 0, st>>>(uoff.p, np, utot.p, 1);
+            BM_CHECK_LAUNCH();
+            uint64_t nu = 0;
+            BM_CUDA(cudaMemcpyAsync(&nu, utot.p, 8, cudaMemcpyDeviceToHost, st));
+            BM_CUDA(cudaStreamSynchronize(st));
+            units.alloc(nu);
+            k_unit_fill<<<grid_for(np), 256, 0, st>>>(cnt.p, uoff.p, np, units.p);
+            BM_CHECK_LAUNCH();
+            n_units = nu;
         }
     }
     if (n_cand) *n_cand = nc;
     E.record(1, st);
-    if (nc) witness_support(S, 3, nc, cand.p, sup.p, st);
+    if (nc) {
+        const View V{reinterpret_cast<const uint32_t *>(S->d_bm.p), S->d_base.p, S->d_rlog.p, S->d_perm.p,
+                     S->d_fail_off.p, S->d_fail_tid.p, S->m, S->n, S->shift};
+        const unsigned grid = (unsigned)std::min<uint64_t>((n_units + 7) / 8, 152ull * 64);
+        k_witness_group<<<grid, 256, 0, st>>>(V, d_pairs, cnt.p, cand.p, units.p, n_units, sup.p);
+        BM_CHECK_LAUNCH();
+    }
     E.record(2, st);
     uint64_t total = 0;
     if (nc) {
