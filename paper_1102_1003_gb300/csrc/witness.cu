@@ -490,8 +490,9 @@ __global__ void __launch_bounds__(256) k_witness_group(View V, const uint32_t *_
             qmax = max(qmax, lim[j]);
         }
         for (uint32_t q = lane; q < qmax; q += 32) {
+            // need_u (bit 6 of every lane): table u < t must be missed by some set
             const uint32_t t = (q >> tq) & 3u;
-            const uint32_t f0 = t >= 1 ? 0u : B6, f1 = t >= 2 ? 0u : B6, f2 = t >= 3 ? 0u : B6;
+            const uint32_t n0 = t >= 1 ? B6 : 0u, n1 = t >= 2 ? B6 : 0u, n2 = t >= 3 ? B6 : 0u;
             const uint4 A = __ldg(&bm4[ca + (q & ma)]);
             const uint4 Bv = __ldg(&bm4[cb + (q & mb)]);
             // all of the unit's column chunks are requested before any is used
@@ -500,31 +501,44 @@ __global__ void __launch_bounds__(256) k_witness_group(View V, const uint32_t *_
             for (uint32_t j = 0; j < GROUP; j++)
                 Cs[j] = q < lim[j] ? __ldg(&bm4[cc[j] + (q & mc[j])]) : make_uint4(0, 0, 0, 0);
             const uint32_t xa[4] = {A.x, A.y, A.z, A.w}, xb[4] = {Bv.x, Bv.y, Bv.z, Bv.w};
-            uint32_t dab[4], nza[4], e0[4], e1[4], e2[4];
+            // What a and b leave to c, per lane: the tables u < t that neither
+            // a nor b misses (u_0, u_1, u_2).  None: c is free; exactly one v:
+            // c must miss v; two or more: no c can make t the witness.  This
+            // becomes an expected byte pat (a's code, v in the top bits where
+            // constrained) under a mask msk, and a validity bit (bit 7) for
+            // lanes where a and b agree on a nonempty code and the rule can hold.
+            uint32_t pat[4], msk[4], msk7[4], val[4];
 #pragma unroll
             for (int k = 0; k < 4; k++) {
-                dab[k] = xa[k] ^ xb[k];
-                nza[k] = ((xa[k] & C6) + C6) & B6;
                 const uint32_t ha = (xa[k] >> 1) & B6, la = xa[k] & B6;
                 const uint32_t hb = (xb[k] >> 1) & B6, lb = xb[k] & B6;
-                e0[k] = (~(ha | la) | ~(hb | lb)) & B6;
-                e1[k] = (~ha & la) | (~hb & lb);
-                e2[k] = (ha & ~la) | (hb & ~lb);
+                const uint32_t u0 = n0 & (ha | la) & (hb | lb);      // neither misses table 0
+                const uint32_t u1 = n1 & ~(~ha & la) & ~(~hb & lb);  // neither misses table 1
+                const uint32_t u2 = n2 & ~(ha & ~la) & ~(hb & ~lb);  // neither misses table 2
+                const uint32_t two = (u0 & u1) | (u0 & u2) | (u1 & u2);
+                const uint32_t q6 = u0 | u1 | u2;
+                pat[k] = (xa[k] & C6) | u1 | (u2 << 1);
+                msk7[k] = C6 | q6;
+                msk[k] = msk7[k] | (q6 << 1);
+                const uint32_t ne = (((xa[k] ^ xb[k]) & C6) + C6) & B6;
+                const uint32_t nz = ((xa[k] & C6) + C6) & B6;
+                val[k] = (nz & ~ne & ~two) << 1;
             }
 #pragma unroll
             for (uint32_t j = 0; j < GROUP; j++) {
                 if (q >= lim[j]) continue;  // also skips the unit's unused slots (lim = 0)
                 const uint32_t xc[4] = {Cs[j].x, Cs[j].y, Cs[j].z, Cs[j].w};
+                uint32_t hits = 0;
 #pragma unroll
                 for (int k = 0; k < 4; k++) {
-                    const uint32_t hc = (xc[k] >> 1) & B6, lc = xc[k] & B6;
-                    const uint32_t diff = dab[k] | (xa[k] ^ xc[k]);
-                    const uint32_t ne = ((diff & C6) + C6) & B6;
-                    const uint32_t E0 = e0[k] | (~(hc | lc) & B6) | f0;
-                    const uint32_t E1 = e1[k] | (~hc & lc) | f1;
-                    const uint32_t E2 = e2[k] | (hc & ~lc) | f2;
-                    cnt[j] += __popc(nza[k] & ~ne & E0 & E1 & E2);
+                    // lane of d is zero iff c matches the expected byte under the mask;
+                    // bit 7 of d7 + 0x7F.. flags a nonzero lane of d7 (no carry leaves a lane)
+                    const uint32_t d = (xc[k] ^ pat[k]) & msk[k];
+                    const uint32_t d7 = (xc[k] ^ pat[k]) & msk7[k];
+                    const uint32_t ok = val[k] & ~((d7 + 0x7F7F7F7Fu) | d);
+                    hits = __dp4a(ok, 0x01010101u, hits);  // 128 per counted slot
                 }
+                cnt[j] += hits >> 7;
             }
         }
 #pragma unroll
