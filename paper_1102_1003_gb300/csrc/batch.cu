@@ -77,7 +77,6 @@ static BatchPlan *make_plan(batmap_set *const *sets, const uint32_t *s, uint32_t
     P->C.resize(k);
     for (uint32_t q = 0; q < k; q++) {
         batmap_set *S = sets[q];
-        const uint64_t n = S->n;
         uint32_t *C = outs[q].d_full;
         if (!C) {
             S->d_C.ensure(S->npairs());
@@ -190,7 +189,6 @@ void autotune(batmap_set *const *sets, uint32_t k, double *eff_out, cudaStream_t
     std::vector<InstView> views;
     for (uint32_t q : idx) {
         batmap_set *S = sets[q];
-        const uint64_t n = S->n;
         S->d_C.ensure(S->npairs());
         views.push_back(InstView{reinterpret_cast<const uint4 *>(S->d_bm.p), S->d_line_off.p, S->d_wshift.p,
                                  S->d_order.p, S->d_C.p, S->n, S->n_a});

@@ -51,7 +51,6 @@ static batmap_status guarded(F &&f) {
 
 // Zero C, run every shape's persistent compare launch over the set's units.
 void enqueue_compare(batmap_set *S, uint32_t *C, const InstView *d_view, cudaStream_t st) {
-    const uint64_t n = S->n;
     const uint64_t npairs = S->npairs();
     if (npairs) BM_CUDA(cudaMemsetAsync(C, 0, npairs * sizeof(uint32_t), st));
     S->d_counters.ensure(1);

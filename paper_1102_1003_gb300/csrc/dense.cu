@@ -97,7 +97,7 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
 constexpr uint32_t IDESC = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(BN >> 3) << 17) |
                            ((uint32_t)(BM >> 4) << 24);
 
-__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t accumulate) {
+__device__ __forceinline__ void umma_e4m3(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t accumulate) {
     asm volatile(
         "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
         "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n"
@@ -159,13 +159,11 @@ k_dense_mmt(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         }
     } else if (warp == 1 && lane == 0) {
         // MMA issuer
-        bool ok = true;
         for (uint32_t it = 0; it < nk; it++) {
             const uint32_t st = it % STAGES, round = it / STAGES;
             if (s_abort || !mbar_wait(smem_addr(&bars[st]), round & 1)) {
                 atomicExch(err, 1);
                 s_abort = 1;
-                ok = false;
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -174,11 +172,10 @@ k_dense_mmt(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 #pragma unroll
             for (int k = 0; k < BK / UMMA_K; k++) {
                 // advance 32 e4m3 = 32 bytes along K inside the swizzled 128-byte rows
-                umma_bf16(tmem, da + (uint64_t)(k * 2), db + (uint64_t)(k * 2), (it > 0 || k > 0) ? 1u : 0u);
+                umma_e4m3(tmem, da + (uint64_t)(k * 2), db + (uint64_t)(k * 2), (it > 0 || k > 0) ? 1u : 0u);
             }
             umma_commit(smem_addr(&bars[STAGES + st]));  // frees the stage when the MMAs have read it
         }
-        (void)ok;
         umma_commit(smem_addr(&bars[2 * STAGES]));  // accumulator ready (or nothing issued)
     } else if (warp >= 2) {
         // epilogue: TMEM lanes 32*(warp % 4) .. +31 hold tile rows of that quarter
@@ -263,7 +260,7 @@ static EncodeTiledFn encode_fn() {
     if (!fn) {
         void *p = nullptr;
         cudaDriverEntryPointQueryResult q;
-        BM_CUDA(cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q));
+        BM_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
         BM_REQUIRE(p && q == cudaDriverEntryPointSuccess, BATMAP_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
         fn = reinterpret_cast<EncodeTiledFn>(p);
     }
