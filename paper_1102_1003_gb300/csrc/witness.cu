@@ -456,7 +456,7 @@ __global__ void __launch_bounds__(256) k_witness_group(View V, const uint32_t *_
                                                        const uint32_t *__restrict__ cand,
                                                        const uint2 *__restrict__ units, uint64_t nu,
                                                        uint32_t *__restrict__ sup) {
-    constexpr uint32_t C6 = 0x3F3F3F3Fu, B6 = 0x40404040u;
+    constexpr uint32_t C6 = 0x3F3F3F3Fu, B6 = 0x40404040u, H7 = 0x80808080u;
     const uint32_t lane = threadIdx.x & 31u;
     const uint4 *bm4 = reinterpret_cast<const uint4 *>(V.bm);
     const uint32_t tq = V.shift - 4;  // 16-byte chunks per table block = r_0 / 16 = 2^(s-4)
@@ -490,9 +490,9 @@ __global__ void __launch_bounds__(256) k_witness_group(View V, const uint32_t *_
             qmax = max(qmax, lim[j]);
         }
         for (uint32_t q = lane; q < qmax; q += 32) {
-            // need_u (bit 6 of every lane): table u < t must be missed by some set
+            // n_u (bit 7 of every lane): table u < t must be missed by some set
             const uint32_t t = (q >> tq) & 3u;
-            const uint32_t n0 = t >= 1 ? B6 : 0u, n1 = t >= 2 ? B6 : 0u, n2 = t >= 3 ? B6 : 0u;
+            const uint32_t n0 = t >= 1 ? H7 : 0u, n1 = t >= 2 ? H7 : 0u, n2 = t >= 3 ? H7 : 0u;
             const uint4 A = __ldg(&bm4[ca + (q & ma)]);
             const uint4 Bv = __ldg(&bm4[cb + (q & mb)]);
             // all of the unit's column chunks are requested before any is used
@@ -507,22 +507,23 @@ __global__ void __launch_bounds__(256) k_witness_group(View V, const uint32_t *_
             // becomes an expected byte pat (a's code, v in the top bits where
             // constrained) under a mask msk, and a validity bit (bit 7) for
             // lanes where a and b agree on a nonempty code and the rule can hold.
+            // The flags live in bit 7 of each lane, where x holds the high bit
+            // of its missing table and x << 1 the low bit.
             uint32_t pat[4], msk[4], msk7[4], val[4];
 #pragma unroll
             for (int k = 0; k < 4; k++) {
-                const uint32_t ha = (xa[k] >> 1) & B6, la = xa[k] & B6;
-                const uint32_t hb = (xb[k] >> 1) & B6, lb = xb[k] & B6;
-                const uint32_t u0 = n0 & (ha | la) & (hb | lb);      // neither misses table 0
-                const uint32_t u1 = n1 & ~(~ha & la) & ~(~hb & lb);  // neither misses table 1
-                const uint32_t u2 = n2 & ~(ha & ~la) & ~(hb & ~lb);  // neither misses table 2
+                const uint32_t a2 = xa[k] << 1, b2 = xb[k] << 1;
+                const uint32_t u0 = n0 & (xa[k] | a2) & (xb[k] | b2);    // neither misses table 0
+                const uint32_t u1 = n1 & (xa[k] | ~a2) & (xb[k] | ~b2);  // neither misses table 1
+                const uint32_t u2 = n2 & (~xa[k] | a2) & (~xb[k] | b2);  // neither misses table 2
                 const uint32_t two = (u0 & u1) | (u0 & u2) | (u1 & u2);
-                const uint32_t q6 = u0 | u1 | u2;
-                pat[k] = (xa[k] & C6) | u1 | (u2 << 1);
-                msk7[k] = C6 | q6;
-                msk[k] = msk7[k] | (q6 << 1);
+                const uint32_t q7 = u0 | u1 | u2;
+                pat[k] = (xa[k] & C6) | (u1 >> 1) | u2;
+                msk7[k] = C6 | (q7 >> 1);
+                msk[k] = msk7[k] | q7;
                 const uint32_t ne = (((xa[k] ^ xb[k]) & C6) + C6) & B6;
                 const uint32_t nz = ((xa[k] & C6) + C6) & B6;
-                val[k] = (nz & ~ne & ~two) << 1;
+                val[k] = ((nz & ~ne) << 1) & ~two;
             }
 #pragma unroll
             for (uint32_t j = 0; j < GROUP; j++) {
