@@ -205,9 +205,9 @@ def dense_leg(args, inst, off, tids, n_out_ref, peaks, peak_kind):
     torch.cuda.synchronize()
     assert k == n_out_ref, (k, n_out_ref)
     elapsed = ev0.elapsed_time(ev1) / 1e3
-    # tensor work actually issued: upper-triangle tiles of 128 x 256 over the padded K
+    # tensor work actually issued: upper-triangle blocks of two 128 x 256 tiles over the padded K
     n, bm, bn = inst.n, 128, 256
-    tiles = sum(min((n + bm - 1) // bm, 2 * bj + 2) for bj in range((n + bn - 1) // bn))
+    tiles = 2 * sum(min((n + 2 * bm - 1) // (2 * bm), bj + 1) for bj in range((n + bn - 1) // bn))
     kpad = (inst.m + 127) // 128 * 128
     flops_issued = 2.0 * tiles * bm * bn * kpad
     flops_alg = 2.0 * npairs * inst.m

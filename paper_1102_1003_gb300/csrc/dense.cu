@@ -5,11 +5,15 @@
 //
 //   * M is materialised as e4m3 {0, 1} bytes (1.0 = 0x38; row = item,
 //     K = transactions, K-major, rows padded to a multiple of 128);
-//   * TMA loads 128 x 128 (A) and 256 x 128 (B) byte tiles into
-//     128-byte-swizzled shared memory through a 4-stage mbarrier ring;
+//   * a CTA computes a 256 x 256 block as two 128 x 256 tiles that share
+//     their B operand: TMA loads two 128 x 128 A tiles and one 256 x 128 B
+//     tile per K step into 128-byte-swizzled shared memory through a
+//     3-stage mbarrier ring (64 KiB per stage; B is read once for both, so
+//     the operand bytes per FLOP are two thirds of a single tile's);
 //   * one thread issues tcgen05.mma.cta_group::1.kind::f8f6f4 (M = 128,
-//     N = 256, K = 32) into an FP32 accumulator in tensor memory;
-//   * four epilogue warps read the accumulator with tcgen05.ld, convert to
+//     N = 256, K = 32) into two FP32 accumulators that fill the 512 columns
+//     of tensor memory;
+//   * four epilogue warps read both accumulators with tcgen05.ld, convert to
 //     integers and add them into the packed upper triangle.
 //
 // Exactness: every product is exactly 0 or 1 and every partial sum an integer
@@ -37,17 +41,17 @@ void enqueue_threshold(uint32_t *C, uint64_t n, uint32_t s, uint32_t *d_pairs, u
 
 namespace dense {
 
-constexpr int BM = 128, BN = 256, BK = 128, STAGES = 4, UMMA_K = 32;
-constexpr uint32_t A_BYTES = BM * BK;          // 16 KiB
+constexpr int BM = 128, BN = 256, BK = 128, STAGES = 3, UMMA_K = 32;
+constexpr uint32_t A_BYTES = BM * BK;          // 16 KiB per A tile (two per stage)
 constexpr uint32_t B_BYTES = BN * BK;          // 32 KiB
-constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr uint32_t TMEM_COLS = 256;            // FP32 accumulator 128 lanes x 256 columns
+constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + B_BYTES;
+constexpr uint32_t TMEM_COLS = 512;            // two FP32 accumulators of 128 lanes x 256 columns
 constexpr int THREADS = 192;                       // warp 0 TMA, warp 1 MMA, warps 2..5 epilogue
 constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
 constexpr uint32_t SPIN_LIMIT = 1u << 26;          // bounded waits (tens of ms per wait)
 
 struct Tile {
-    uint32_t bi, bj;  // row block (128 rows), column block (256 columns)
+    uint32_t bp, bj;  // row blocks 2 bp and 2 bp + 1 (128 rows each), column block bj (256 columns)
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -152,10 +156,11 @@ k_dense_mmt(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             }
             const uint32_t full = smem_addr(&bars[st]);
             uint8_t *sa = smem + st * STAGE_BYTES;
-            mbar_expect_tx(full, STAGE_BYTES);
+            mbar_expect_tx(full, STAGE_BYTES);  // rows past the matrix are zero-filled and counted
             const int kx = (int)((kb0 + it) * BK);
-            tma_load_2d(smem_addr(sa), &tmA, full, kx, (int)(tile.bi * BM));
-            tma_load_2d(smem_addr(sa + A_BYTES), &tmB, full, kx, (int)(tile.bj * BN));
+            tma_load_2d(smem_addr(sa), &tmA, full, kx, (int)(2 * tile.bp * BM));
+            tma_load_2d(smem_addr(sa + A_BYTES), &tmA, full, kx, (int)((2 * tile.bp + 1) * BM));
+            tma_load_2d(smem_addr(sa + 2 * A_BYTES), &tmB, full, kx, (int)(tile.bj * BN));
         }
     } else if (warp == 1 && lane == 0) {
         // MMA issuer
@@ -168,11 +173,13 @@ k_dense_mmt(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t a0 = smem_addr(smem + st * STAGE_BYTES);
-            const uint64_t da = smem_desc(a0), db = smem_desc(a0 + A_BYTES);
+            const uint64_t da0 = smem_desc(a0), da1 = smem_desc(a0 + A_BYTES), db = smem_desc(a0 + 2 * A_BYTES);
 #pragma unroll
             for (int k = 0; k < BK / UMMA_K; k++) {
                 // advance 32 e4m3 = 32 bytes along K inside the swizzled 128-byte rows
-                umma_e4m3(tmem, da + (uint64_t)(k * 2), db + (uint64_t)(k * 2), (it > 0 || k > 0) ? 1u : 0u);
+                const uint32_t acc = (it > 0 || k > 0) ? 1u : 0u;
+                umma_e4m3(tmem, da0 + (uint64_t)(k * 2), db + (uint64_t)(k * 2), acc);
+                umma_e4m3(tmem + (uint32_t)BN, da1 + (uint64_t)(k * 2), db + (uint64_t)(k * 2), acc);
             }
             umma_commit(smem_addr(&bars[STAGES + st]));  // frees the stage when the MMAs have read it
         }
@@ -187,8 +194,10 @@ k_dense_mmt(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             s_abort = 1;
         } else if (!s_abort && nk > 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t gi = tile.bi * BM + q * 32 + lane;
             const uint64_t nn = n;
+#pragma unroll 1
+            for (int h = 0; h < 2; h++) {
+            const uint32_t gi = (2 * tile.bp + h) * BM + q * 32 + lane;
 #pragma unroll 1
             for (int c0 = 0; c0 < BN; c0 += 32) {
                 uint32_t v[32];
@@ -201,7 +210,7 @@ k_dense_mmt(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                       "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
                       "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
                       "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-                    : "r"(tmem + ((q * 32u) << 16) + (uint32_t)c0));
+                    : "r"(tmem + ((q * 32u) << 16) + (uint32_t)(h * BN + c0)));
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                 if (gi < n) {
 #pragma unroll
@@ -212,6 +221,7 @@ k_dense_mmt(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                             atomicAdd(&C[(uint64_t)gi * nn - (uint64_t)gi * (gi + 1) / 2 + (gj - gi - 1)], cnt);
                     }
                 }
+            }
             }
         }
     }
@@ -335,11 +345,12 @@ void run_dense(uint32_t m, uint32_t n, const uint64_t *d_off, const uint32_t *d_
     }
     W.ev.record(1, st);
     if (npairs) BM_CUDA(cudaMemsetAsync(C, 0, npairs * sizeof(uint32_t), st));
-    // upper-triangle tiles: row block bi (128 rows) holds a pair i < j with column block bj (256)
+    // upper-triangle blocks: row blocks 2 bp, 2 bp + 1 (128 rows each) hold a pair i < j with
+    // column block bj (256) iff bp <= bj; the second row block may lie past n (zero rows)
     std::vector<Tile> tl;
-    const uint32_t nbi = (n + BM - 1) / BM, nbj = (n + BN - 1) / BN;
+    const uint32_t nbp = (n + 2 * BM - 1) / (2 * BM), nbj = (n + BN - 1) / BN;
     for (uint32_t bj = 0; bj < nbj; bj++)
-        for (uint32_t bi = 0; bi < nbi && bi <= 2 * bj + 1; bi++) tl.push_back({bi, bj});
+        for (uint32_t bp = 0; bp < nbp && bp <= bj; bp++) tl.push_back({bp, bj});
     const uint32_t kblocks = (uint32_t)(ld / BK);
     if (!tl.empty()) {
         int dev = 0, nsm = 0;
