@@ -173,7 +173,27 @@ def _stream_handle(stream):
 
 
 def _ptr(t):
-    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+    """Device pointer of a contiguous CUDA tensor of 4- or 8-byte elements (None -> NULL).
+    The library reads raw memory, so a strided view or a host tensor is refused here."""
+    if t is None:
+        return ctypes.c_void_p(0)
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    if t.element_size() not in (4, 8):
+        raise ValueError(f"expected 4- or 8-byte elements, got {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _check_inputs(offsets, tids, perm=None):
+    """CSR offsets are 8-byte, tids and permutations 4-byte elements (the ABI's uint64 / uint32)."""
+    if offsets.element_size() != 8:
+        raise ValueError(f"offsets must hold 8-byte integers, got {offsets.dtype}")
+    if tids.element_size() != 4:
+        raise ValueError(f"tids must hold 4-byte integers, got {tids.dtype}")
+    if perm is not None and perm.element_size() != 4:
+        raise ValueError(f"perm must hold 4-byte integers, got {perm.dtype}")
 
 
 def batmap_default_params(**overrides) -> batmap_params:
@@ -210,6 +230,9 @@ def batmap_build(m: int, offsets, tids, perm, params: batmap_params | None = Non
 
     offsets: cuda uint64 (int64) tensor [n+1]; tids: cuda int32/uint32 [T];
     perm: cuda int32/uint32 [3, m] (three permutations of [0, m))."""
+    _check_inputs(offsets, tids, perm)
+    if int(m) >= 1 and int(perm.numel()) != 3 * int(m):
+        raise ValueError(f"perm must hold 3 rows of m = {m} entries")
     L = load_library()
     n = int(offsets.numel()) - 1
     h = ctypes.c_void_p()
@@ -223,6 +246,9 @@ def batmap_build_cross(m: int, n_a: int, offsets, tids, perm, params: batmap_par
                        stream=None) -> BatMapSet:
     """Cross-mode set: the CSR holds n_a sets of family A then the sets of family B;
     pair_support_all then reports the n_a x n_b supports |A_i cap B_j|."""
+    _check_inputs(offsets, tids, perm)
+    if int(m) >= 1 and int(perm.numel()) != 3 * int(m):
+        raise ValueError(f"perm must hold 3 rows of m = {m} entries")
     L = load_library()
     n = int(offsets.numel()) - 1
     h = ctypes.c_void_p()
@@ -239,9 +265,10 @@ def batmap_build_d(d: int, m: int, offsets, tids, perm, params: batmap_params | 
                    stream=None) -> BatMapSet:
     """d-of-(d+1) BatMaps (Sec. V generalisation): d = 2 is batmap_build; d = 3 builds
     3-of-4 BatMaps for itemset_support / frequent_triples.  perm: cuda [d+1, m]."""
+    _check_inputs(offsets, tids, perm)
     L = load_library()
     n = int(offsets.numel()) - 1
-    if d in (2, 3) and int(perm.numel()) != (d + 1) * int(m):
+    if d in (2, 3) and int(m) >= 1 and int(perm.numel()) != (d + 1) * int(m):
         raise ValueError(f"perm must hold {d + 1} rows of m = {m} entries")
     h = ctypes.c_void_p()
     pp = ctypes.byref(params) if params is not None else None
@@ -350,6 +377,7 @@ def pair_support_all(bset: BatMapSet, s: int, pairs=None, full=None, stream=None
 def pair_support_dense(m: int, offsets, tids, s: int, pairs=None, full=None, stream=None):
     """Dense-bitmap tensor-core path; returns (n_out, pairs view, timing dict)."""
     import torch
+    _check_inputs(offsets, tids)
     L = load_library()
     n = int(offsets.numel()) - 1
     n_out = ctypes.c_uint64(0)
@@ -445,6 +473,9 @@ class BatMapPool:
 
 
 def batmap_pool_create(m: int, offsets, tids, perm, params: batmap_params | None = None, stream=None) -> BatMapPool:
+    _check_inputs(offsets, tids, perm)
+    if int(m) >= 1 and int(perm.numel()) != 3 * int(m):
+        raise ValueError(f"perm must hold 3 rows of m = {m} entries")
     L = load_library()
     n = int(offsets.numel()) - 1
     h = ctypes.c_void_p()

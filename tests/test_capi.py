@@ -72,3 +72,22 @@ def _load_missing(batmap, tmp_path):
         batmap.load_library(str(tmp_path / "libbatmap_missing.so"))
     finally:
         batmap._lib = saved
+
+
+def test_binding_refuses_malformed_tensors(lib):
+    # checked before any device call, so this runs without a GPU
+    import torch
+    from paper_1102_1003_gb300 import batmap
+    off = torch.tensor([0, 2], dtype=torch.int64)
+    tids = torch.tensor([1, 3], dtype=torch.int32)
+    perm = torch.arange(30, dtype=torch.int32).reshape(3, 10) % 10
+    with pytest.raises(ValueError):
+        batmap.batmap_build(10, off, tids.to(torch.int64), perm)          # 8-byte tids
+    with pytest.raises(ValueError):
+        batmap.batmap_build(10, off.to(torch.int32), tids, perm)          # 4-byte offsets
+    with pytest.raises(ValueError):
+        batmap.batmap_build(10, off, tids, perm[:2])                      # two permutation rows
+    with pytest.raises(ValueError):
+        batmap.batmap_build_d(3, 10, off, tids, perm)                     # d = 3 needs four rows
+    with pytest.raises(ValueError):
+        batmap.batmap_build(10, off, tids, perm)                          # host tensors
