@@ -40,11 +40,11 @@ import datagen  # noqa: E402
 METRIC = "item-pair supports/sec and achieved HBM GB/s, batched vs plain, bit-exact"
 UNIT = "pair-supports/s"
 WORKLOAD_DESC = {
-    "cfg1": "plain frequent pair mining, m=10,000, n=200, Bernoulli p=0.05, s=25",
-    "cfg2": "plain all-pairs mining, m=1,000,000, n=2,000, Zipf(1) items at mean density 2%, s=1,000",
-    "cfg4_0.1": "density sweep, m=4,194,304, n=8,192, Bernoulli p=0.001",
-    "cfg4_1": "density sweep, m=4,194,304, n=8,192, Bernoulli p=0.01",
-    "cfg4_5": "density sweep, m=4,194,304, n=8,192, Bernoulli p=0.05",
+    "bern_m10k_n200": "plain frequent pair mining, m=10,000, n=200, Bernoulli p=0.05, s=25",
+    "zipf_m1m_n2000": "plain all-pairs mining, m=1,000,000, n=2,000, Zipf(1) items at mean density 2%, s=1,000",
+    "bern_m4m_n8192_p0.1": "density sweep, m=4,194,304, n=8,192, Bernoulli p=0.001",
+    "bern_m4m_n8192_p1": "density sweep, m=4,194,304, n=8,192, Bernoulli p=0.01",
+    "bern_m4m_n8192_p5": "density sweep, m=4,194,304, n=8,192, Bernoulli p=0.05",
 }
 OPS_PER_WORD_PAIR = 4  # LOP3, IADD, LOP3, IDP4A per 32-bit word pair
 WITNESS_OPS = 5        # per word-triple against the pair's prepared pattern: 2 masked XORs, IADD, AND-NOT, IDP4A
@@ -768,7 +768,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["mine", "reference"], default="mine")
-    ap.add_argument("--workload", choices=sorted(WORKLOAD_DESC) + ["serve", "batch", "nsweep", "cross", "triples"], default="cfg2")
+    ap.add_argument("--workload", choices=sorted(WORKLOAD_DESC) + ["serve", "batch", "nsweep", "cross", "triples"], default="zipf_m1m_n2000")
     ap.add_argument("--nsweep", type=int, nargs="+", default=[1000, 2000, 4000, 8000, 16000, 32000, 64000])
     ap.add_argument("--instances", type=int, default=64, help="instances (batch workload)")
     ap.add_argument("--no-autotune", action="store_true")
@@ -787,7 +787,7 @@ def main():
             {"serve": run_serve, "batch": run_batch, "nsweep": run_nsweep, "cross": run_cross,
              "triples": run_triples}[args.workload](args)
         return
-    inst = datagen.config_instance(args.workload)
+    inst = datagen.workload_instance(args.workload)
     if args.impl == "reference":
         run_reference(args, inst, rank, world)
     else:

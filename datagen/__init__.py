@@ -30,9 +30,9 @@ import numpy as np
 
 __all__ = [
     "Instance", "bernoulli_item", "bernoulli_tidlists", "zipf_probabilities",
-    "zipf_tidlists", "permutations", "config_instance", "batch_specs",
+    "zipf_tidlists", "permutations", "workload_instance", "batch_specs",
     "pool_sizes", "pool_tidlists", "from_lists", "transactions_to_tidlists",
-    "CONFIGS", "concat", "cross_instance", "triples_instance",
+    "WORKLOADS", "concat", "cross_instance", "triples_instance",
 ]
 
 
@@ -94,7 +94,7 @@ def from_lists(lists, m: int, s: int = 0, name: str = "") -> Instance:
 
 
 def bernoulli_tidlists(m: int, n: int, p: float, seed: int, s: int = 0, name: str = "") -> Instance:
-    """Uniform density p for every item (configs 1 and 4)."""
+    """Uniform density p for every item (the Bernoulli workloads)."""
     return from_lists([bernoulli_item(_item_rng(seed, i), m, p) for i in range(n)], m, s, name)
 
 
@@ -117,7 +117,7 @@ def zipf_probabilities(n: int, density: float, exponent: float = 1.0) -> np.ndar
 
 def zipf_tidlists(m: int, n: int, density: float, seed: int, exponent: float = 1.0,
                   s: int = 0, name: str = "") -> Instance:
-    """Zipf-skewed item frequencies with mean density `density` (configs 2, 3)."""
+    """Zipf-skewed item frequencies with mean density `density` (the Zipf and batched workloads)."""
     probs = zipf_probabilities(n, density, exponent)
     rank_of_item = np.random.default_rng([int(seed), 0x5A1F]).permutation(n)
     lists = [bernoulli_item(_item_rng(seed, i), m, float(probs[rank_of_item[i]]))
@@ -145,18 +145,18 @@ def permutations(m: int, seed: int, count: int = 3) -> np.ndarray:
 
 # ---- the five workload configurations -------------------------------------
 
-CONFIGS = {
-    "cfg1": dict(kind="bernoulli", m=10_000, n=200, p=0.05, s=25, seed=1),
-    "cfg2": dict(kind="zipf", m=1_000_000, n=2_000, density=0.02, s=1_000, seed=2),
-    "cfg4_0.1": dict(kind="bernoulli", m=4_194_304, n=8_192, p=0.001, s=4_195, seed=41),
-    "cfg4_1": dict(kind="bernoulli", m=4_194_304, n=8_192, p=0.01, s=4_195, seed=42),
-    "cfg4_5": dict(kind="bernoulli", m=4_194_304, n=8_192, p=0.05, s=4_195, seed=43),
+WORKLOADS = {
+    "bern_m10k_n200": dict(kind="bernoulli", m=10_000, n=200, p=0.05, s=25, seed=1),
+    "zipf_m1m_n2000": dict(kind="zipf", m=1_000_000, n=2_000, density=0.02, s=1_000, seed=2),
+    "bern_m4m_n8192_p0.1": dict(kind="bernoulli", m=4_194_304, n=8_192, p=0.001, s=4_195, seed=41),
+    "bern_m4m_n8192_p1": dict(kind="bernoulli", m=4_194_304, n=8_192, p=0.01, s=4_195, seed=42),
+    "bern_m4m_n8192_p5": dict(kind="bernoulli", m=4_194_304, n=8_192, p=0.05, s=4_195, seed=43),
 }
 
 
-def config_instance(name: str, scale_n: int | None = None) -> Instance:
-    """Instance for a named configuration; `scale_n` truncates the item count."""
-    c = CONFIGS[name]
+def workload_instance(name: str, scale_n: int | None = None) -> Instance:
+    """Instance of a named workload; `scale_n` truncates the item count."""
+    c = WORKLOADS[name]
     n = c["n"] if scale_n is None else min(c["n"], scale_n)
     if c["kind"] == "bernoulli":
         return bernoulli_tidlists(c["m"], n, c["p"], c["seed"], c["s"], name)

@@ -49,8 +49,8 @@ def test_dense_small_ragged():
     _check(datagen.bernoulli_tidlists(3001, 131, 0.07, seed=3, s=10))
 
 
-def test_dense_config1():
-    _check(datagen.config_instance("cfg1"))
+def test_dense_bernoulli_m10k():
+    _check(datagen.workload_instance("bern_m10k_n200"))
 
 
 @pytest.mark.parametrize("n", [1, 2, 255, 257, 600])
@@ -64,18 +64,18 @@ def test_dense_empty_and_full_items():
     _check(datagen.from_lists(lists, m, s=1))
 
 
-def test_dense_config2_full_scale_exact():
-    """Configuration 2: supports up to ~10^6, i.e. FP32 accumulation carries
+def test_dense_zipf_full_scale_exact():
+    """The m = 10^6, n = 2,000 Zipf workload: supports up to ~10^6, i.e. FP32 accumulation carries
     20-bit integers exactly."""
-    inst = datagen.config_instance("cfg2")
+    inst = datagen.workload_instance("zipf_m1m_n2000")
     _check(inst)
 
 
-@pytest.mark.parametrize("name", ["cfg4_1", "cfg4_5"])
-def test_dense_config4_full_scale_sampled(name):
-    """Configuration 4 at full size on the tensor-core path: sampled supports
+@pytest.mark.parametrize("name", ["bern_m4m_n8192_p1", "bern_m4m_n8192_p5"])
+def test_dense_density_sweep_full_scale_sampled(name):
+    """The m = 4,194,304, n = 8,192 Bernoulli workloads at full size on the tensor-core path: sampled supports
     against the merge oracle and whole rows through the row-sum invariant."""
-    inst = datagen.config_instance(name)
+    inst = datagen.workload_instance(name)
     full, n_out, pairs, _ = _dense(inst)
     n = inst.n
     rng = np.random.default_rng(21)

@@ -39,8 +39,8 @@ def _check_exact(inst, full, n_out, pairs, s=None):
     assert np.array_equal(pairs, ref_pairs)
 
 
-def test_config1_all_pairs_exact():
-    inst = datagen.config_instance("cfg1")
+def test_bernoulli_m10k_all_pairs_exact():
+    inst = datagen.workload_instance("bern_m10k_n200")
     full, n_out, pairs, bset = run_all_pairs(inst, perm_seed=1)
     assert inst.n * (inst.n - 1) // 2 == 19_900
     _check_exact(inst, full, n_out, pairs)
@@ -48,8 +48,8 @@ def test_config1_all_pairs_exact():
     assert np.array_equal(pairs, oracle.pairs_threshold(inst.offsets, inst.tids, inst.s))
 
 
-def test_config1_layout_valid():
-    inst = datagen.config_instance("cfg1")
+def test_bernoulli_m10k_layout_valid():
+    inst = datagen.workload_instance("bern_m10k_n200")
     _, _, _, bset = run_all_pairs(inst, perm_seed=1, want_full=False)
     assert layout_errors(inst, bset, 1) == []
     info = bset.info
@@ -134,7 +134,7 @@ def test_edge_cases(case):
 def test_threshold_extremes_and_capacity():
     import torch
     import paper_1102_1003_gb300 as pkg
-    inst = datagen.config_instance("cfg1")
+    inst = datagen.workload_instance("bern_m10k_n200")
     off, tids, perm = device_inputs(inst, 0)
     bset = pkg.batmap_build(inst.m, off, tids, perm)
     ref = oracle.pairs_full(inst.offsets, inst.tids, threads=THREADS)
@@ -218,23 +218,23 @@ def test_batch_equals_separate_calls():
             assert np.array_equal(fulls[q][:refs[q].size].cpu().numpy().astype(np.uint32), refs[q])
 
 
-def test_config2_full_scale_exact():
-    """Configuration 2 at full size (m = 10^6, n = 2000, Zipf, 2% density):
+def test_zipf_full_scale_exact():
+    """The Zipf workload at full size (m = 10^6, n = 2000, Zipf, 2% density):
     every one of the 1,999,000 supports against the merge oracle."""
-    inst = datagen.config_instance("cfg2")
+    inst = datagen.workload_instance("zipf_m1m_n2000")
     full, n_out, pairs, bset = run_all_pairs(inst, perm_seed=2)
     _check_exact(inst, full, n_out, pairs)
     info = bset.info
     assert info["n_classes"] >= 6
 
 
-@pytest.mark.parametrize("name", ["cfg4_0.1", "cfg4_1", "cfg4_5"])
-def test_config4_full_scale_sampled(name):
-    """Configuration 4 at full size (m = 4,194,304, n = 8,192, 33.5M pairs) in
+@pytest.mark.parametrize("name", ["bern_m4m_n8192_p0.1", "bern_m4m_n8192_p1", "bern_m4m_n8192_p5"])
+def test_density_sweep_full_scale_sampled(name):
+    """The density sweep at full size (m = 4,194,304, n = 8,192, 33.5M pairs) in
     the bench's launch configuration: 3000 sampled supports against the merge
     oracle, whole rows through the row-sum invariant, and the frequent-pair
     list against the supports."""
-    inst = datagen.config_instance(name)
+    inst = datagen.workload_instance(name)
     full, n_out, pairs, bset = run_all_pairs(inst, perm_seed=4)
     n = inst.n
     rng = np.random.default_rng(12)

@@ -130,11 +130,11 @@ def _oracle_triples(inst, s):
     return pairs, cand, np.concatenate([cand[keep], sup[keep, None].astype(np.uint32)], axis=1)
 
 
-@pytest.mark.parametrize("name,s", [("cfg1", 25), ("dense", 40), ("zipf", 60)])
+@pytest.mark.parametrize("name,s", [("bern_m10k_n200", 25), ("dense", 40), ("zipf", 60)])
 def test_frequent_triples_exact(name, s):
     import torch
     import paper_1102_1003_gb300 as pkg
-    inst = {"cfg1": lambda: datagen.config_instance("cfg1"),           # no frequent triple at s = 25
+    inst = {"bern_m10k_n200": lambda: datagen.workload_instance("bern_m10k_n200"),           # no frequent triple at s = 25
             "dense": lambda: datagen.bernoulli_tidlists(2_000, 60, 0.3, seed=6),
             "zipf": lambda: datagen.zipf_tidlists(50_000, 300, 0.03, seed=5)}[name]()
     pairs_ref, cand, want = _oracle_triples(inst, s)
@@ -160,7 +160,7 @@ def test_frequent_triples_exact(name, s):
 def test_unsorted_pairs_rejected():
     import torch
     import paper_1102_1003_gb300 as pkg
-    inst = datagen.config_instance("cfg1")
+    inst = datagen.workload_instance("bern_m10k_n200")
     b3 = _build(inst, 1)
     bad = torch.tensor([[3, 4, 30], [1, 2, 30]], dtype=torch.int32, device="cuda")
     with pytest.raises(pkg.BatmapError):

@@ -68,7 +68,7 @@ def test_merge_matches_python_sets():
 
 def test_merge_matches_transaction_scan():
     # configuration-1 sized instance: m = 10,000, n = 200, p = 0.05
-    inst = datagen.config_instance("cfg1")
+    inst = datagen.workload_instance("bern_m10k_n200")
     n = inst.n
     # horizontal form: transaction x -> items containing it
     trans = [[] for _ in range(inst.m)]
@@ -110,7 +110,7 @@ def test_invariants():
 
 
 def test_threshold_is_filtered_full_matrix():
-    inst = datagen.config_instance("cfg1")
+    inst = datagen.workload_instance("bern_m10k_n200")
     full = oracle.pairs_full(inst.offsets, inst.tids)
     for s in (0, 1, 25, 30, 10**9):
         trip = oracle.pairs_threshold(inst.offsets, inst.tids, s)
@@ -152,7 +152,7 @@ def test_kway_matches_python_sets():
 
 
 def test_generators_are_valid_csr():
-    for inst in (datagen.config_instance("cfg1"), datagen.zipf_tidlists(100000, 300, 0.02, 5),
+    for inst in (datagen.workload_instance("bern_m10k_n200"), datagen.zipf_tidlists(100000, 300, 0.02, 5),
                  datagen.pool_tidlists(200, 2**20, 10, 10**5, 3)):
         assert inst.offsets[0] == 0 and (np.diff(inst.offsets.astype(np.int64)) >= 0).all()
         for i in range(inst.n):
