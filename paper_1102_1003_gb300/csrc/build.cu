@@ -289,6 +289,56 @@ DevBuf<uint32_t> &scratch_table(uint64_t slots) {
 void release_scratch() {
     std::lock_guard<std::mutex> lock(g_scratch_mu);
     g_scratch.release();
+    bm_buffer_release_all();
+}
+
+// ---- cache of BatMap arrays ----------------------------------------------------------
+
+namespace {
+struct CachedBuf {
+    uint8_t *p;
+    size_t cap;
+};
+std::mutex g_bm_cache_mu;
+std::vector<CachedBuf> g_bm_cache;  // at most two, oldest first
+}  // namespace
+
+uint8_t *bm_buffer_take(size_t bytes, size_t *capacity) {
+    {
+        std::lock_guard<std::mutex> lock(g_bm_cache_mu);
+        int best = -1;
+        for (int i = 0; i < (int)g_bm_cache.size(); i++) {
+            const size_t c = g_bm_cache[i].cap;
+            if (c >= bytes && c <= 2 * bytes + (64ull << 20) && (best < 0 || c < g_bm_cache[best].cap)) best = i;
+        }
+        if (best >= 0) {
+            const CachedBuf b = g_bm_cache[best];
+            g_bm_cache.erase(g_bm_cache.begin() + best);
+            *capacity = b.cap;
+            return b.p;
+        }
+    }
+    uint8_t *p = nullptr;
+    BM_CUDA(cudaMalloc(&p, bytes));
+    *capacity = bytes;
+    return p;
+}
+
+void bm_buffer_give(uint8_t *p, size_t capacity) {
+    // no queued work may still use the array when it is handed out again
+    cudaDeviceSynchronize();
+    std::lock_guard<std::mutex> lock(g_bm_cache_mu);
+    g_bm_cache.push_back({p, capacity});
+    if (g_bm_cache.size() > 2) {
+        cudaFree(g_bm_cache.front().p);
+        g_bm_cache.erase(g_bm_cache.begin());
+    }
+}
+
+void bm_buffer_release_all() {
+    std::lock_guard<std::mutex> lock(g_bm_cache_mu);
+    for (auto &b : g_bm_cache) cudaFree(b.p);
+    g_bm_cache.clear();
 }
 
 void build_set(batmap_set *S, const uint64_t *d_offsets, const uint32_t *d_tids,

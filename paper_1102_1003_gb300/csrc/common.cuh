@@ -72,6 +72,33 @@ struct DevBuf {
     size_t bytes() const { return n * sizeof(T); }
 };
 
+// The BatMap array of a built set comes from a small cache: a freed set's
+// array (after a device synchronisation, as cudaFree would do) is kept for the
+// next build, at most two arrays, reused when no larger than twice the request
+// plus 64 MiB, so repeated builds do not map and unmap hundreds of MB each.
+uint8_t *bm_buffer_take(size_t bytes, size_t *capacity);
+void bm_buffer_give(uint8_t *p, size_t capacity);
+void bm_buffer_release_all();
+
+struct BmBuf {
+    uint8_t *p = nullptr;
+    size_t n = 0, cap = 0;
+    BmBuf() = default;
+    BmBuf(const BmBuf &) = delete;
+    BmBuf &operator=(const BmBuf &) = delete;
+    ~BmBuf() { release(); }
+    void alloc(size_t bytes) {
+        release();
+        if (bytes) p = bm_buffer_take(bytes, &cap);
+        n = bytes;
+    }
+    void release() {
+        if (p) bm_buffer_give(p, cap);
+        p = nullptr;
+        n = cap = 0;
+    }
+};
+
 // Events bracketing phases of a call on its stream.
 struct PhaseEvents {
     static constexpr int N = 8;
@@ -175,7 +202,7 @@ struct batmap_set {
     std::vector<bm::WorkUnit> units;      // compare schedule, longest first
 
     // device data
-    bm::DevBuf<uint8_t> d_bm;             // all BatMaps, width-sorted order
+    bm::BmBuf d_bm;                       // all BatMaps, width-sorted order
     bm::DevBuf<uint32_t> d_line_off;      // [n] sorted
     bm::DevBuf<uint32_t> d_wshift;        // [n] sorted
     bm::DevBuf<uint32_t> d_order;         // [n]
