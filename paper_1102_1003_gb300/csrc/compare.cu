@@ -225,15 +225,20 @@ __device__ __forceinline__ void process_unit(uint4 *smem, const InstView &V, con
 // conflict-free); one block barrier per COL_CK steps publishes a column stage
 // and frees the oldest.  The wrap of a narrower row is an incremental index
 // reset.
-constexpr int DIRECT_DEPTH = 4;  // per-thread row ring (16-byte chunks, DEPTH-1 steps ahead)
-constexpr int COL_CK = 8;        // column chunks per stage (32 words)
+// Per-thread row ring depth (16-byte chunks, DEPTH-1 steps ahead): as deep as
+// the shared memory allows, 6 steps for 8 rows per thread (192 KiB), 8 for 4.
+constexpr int DEPTH_MR8 = 6, DEPTH_MR4 = 8;
+constexpr int direct_depth(int MR) { return MR >= 8 ? DEPTH_MR8 : DEPTH_MR4; }
+constexpr int COL_CK = 32;       // column chunks per stage (128 words)
 constexpr int COL_STAGES = 3;    // column stages in flight
-static_assert(2 * COL_CK >= DIRECT_DEPTH, "column copies must retire before their stage is read");
+static_assert(2 * COL_CK >= DEPTH_MR8 && 2 * COL_CK >= DEPTH_MR4,
+              "column copies must retire before their stage is read");
 
 template <int TR_T, int TC_T, int MC, int MR, bool STAGE_COLS>
 struct DirectTile {
     static constexpr int TC = TC_T * MC;
-    static constexpr int ROW_CHUNKS = DIRECT_DEPTH * MR * 256;
+    static constexpr int DEPTH = direct_depth(MR);
+    static constexpr int ROW_CHUNKS = DEPTH * MR * 256;
     static constexpr int COL_STAGE = COL_CK * TC;
     static constexpr int FILL = STAGE_COLS ? (COL_STAGE + 255) / 256 : 1;  // column chunks copied per thread
     // the dynamic shared memory of the kernel is the maximum over shapes and
@@ -307,7 +312,7 @@ __device__ __forceinline__ void process_unit_direct(uint4 *smem, const InstView 
         for (int b = 0; b < MC; b++) acc[a][b] = 0;
 
     auto issue_rows = [&](uint32_t step) {
-        uint4 *slot = smem + (size_t)(step % DIRECT_DEPTH) * MR * 256 + tid;
+        uint4 *slot = smem + (size_t)(step % T::DEPTH) * MR * 256 + tid;
 #pragma unroll
         for (int a = 0; a < MR; a++) {
             const bool ok = rbase[a] != 0xFFFFFFFFu;
@@ -327,7 +332,7 @@ __device__ __forceinline__ void process_unit_direct(uint4 *smem, const InstView 
             if ((uint32_t)st < nstage) fill_cols(st);
     }
 #pragma unroll
-    for (int d = 0; d < DIRECT_DEPTH - 1; d++) {
+    for (int d = 0; d < T::DEPTH - 1; d++) {
         if ((uint32_t)d < nq) issue_rows(d);
         cp_async_commit();
     }
@@ -346,7 +351,7 @@ __device__ __forceinline__ void process_unit_direct(uint4 *smem, const InstView 
             // the same retirement point as DEPTH-1 after it
             const uint32_t s = q / COL_CK, kq = q % COL_CK;
             if (kq == 0) {
-                cp_async_wait<DIRECT_DEPTH - 2>();
+                cp_async_wait<T::DEPTH - 2>();
                 __syncthreads();  // column stage s is complete; stage s-1 is no longer read
                 if (s + COL_STAGES - 1 < nstage) fill_cols(s + COL_STAGES - 1);
             }
@@ -356,7 +361,7 @@ __device__ __forceinline__ void process_unit_direct(uint4 *smem, const InstView 
 #pragma unroll
             for (int b = 0; b < MC; b++) Y[b] = cs[TC_T * b];
         }
-        if (q + DIRECT_DEPTH - 1 < nq) issue_rows(q + DIRECT_DEPTH - 1);
+        if (q + T::DEPTH - 1 < nq) issue_rows(q + T::DEPTH - 1);
         cp_async_commit();
         uint4 Yn[MC];
         if constexpr (!STAGE_COLS) {
@@ -365,9 +370,9 @@ __device__ __forceinline__ void process_unit_direct(uint4 *smem, const InstView 
             for (int b = 0; b < MC; b++)
                 Yn[b] = (more && cbase[b] != 0xFFFFFFFFu) ? __ldg(bm + (size_t)cbase[b] + q + 1) : zero;
         }
-        cp_async_wait<DIRECT_DEPTH - 1>();
+        cp_async_wait<T::DEPTH - 1>();
         uint4 X[MR];
-        const uint4 *slot = smem + (size_t)(q % DIRECT_DEPTH) * MR * 256 + tid;
+        const uint4 *slot = smem + (size_t)(q % T::DEPTH) * MR * 256 + tid;
 #pragma unroll
         for (int a = 0; a < MR; a++) X[a] = slot[a * 256];
 #pragma unroll
