@@ -3,13 +3,13 @@
 // bitmaps is the dense boolean contraction C = M M^T with M in {0,1}^(n x m)
 // (items x transactions), so it runs on the 5th-generation tensor cores:
 //
-//   * M is materialised as e4m3 {0, 1} bytes (1.0 = 0x38; row = item,
-//     K = transactions, K-major, rows padded to a multiple of 128);
-//   * a CTA computes a 256 x 256 block as two 128 x 256 tiles that share
-//     their B operand: TMA loads two 128 x 128 A tiles and one 256 x 128 B
-//     tile per K step into 128-byte-swizzled shared memory through a
-//     3-stage mbarrier ring (64 KiB per stage; B is read once for both, so
-//     the operand bytes per FLOP are two thirds of a single tile's);
+//   * M stays packed in HBM, one bit per (item, transaction), rows padded to
+//     a multiple of 128 bits (n m / 8 bytes: 4.3 GB at n = 8,192, m = 2^22);
+//   * a CTA computes a 256 x 256 block as two 128 x 256 tiles sharing their B
+//     operand; per K step of 128 transactions, TMA loads the 512 rows' bits
+//     (8 KiB) into a 3-stage ring, sixteen expander warps turn them into e4m3
+//     {0, 1} bytes (1.0 = 0x38) in the 128-byte-swizzled layout the MMA reads
+//     (64 KiB, 3-stage ring) and publish each stage after a proxy fence;
 //   * one thread issues tcgen05.mma.cta_group::1.kind::f8f6f4 (M = 128,
 //     N = 256, K = 32) into two FP32 accumulators that fill the 512 columns
 //     of tensor memory;
@@ -20,7 +20,7 @@
 // below 2^24, which the FP32 accumulator represents exactly (the tests check
 // bit-exactness at supports up to 10^6); INT8 MMA (kind::i8) is not available
 // on sm_103a.  Split-K partial sums are added with integer atomics (exact in
-// any order).  Only tiles that hold a pair i < j are computed.
+// any order).  Only blocks that hold a pair i < j are computed.
 //
 // Every mbarrier wait is bounded; on timeout the kernel records an error
 // flag, stops issuing work, waits (bounded) for what it issued, frees its
@@ -46,8 +46,12 @@ constexpr uint32_t A_BYTES = BM * BK;          // 16 KiB per A tile (two per sta
 constexpr uint32_t B_BYTES = BN * BK;          // 32 KiB
 constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + B_BYTES;
 constexpr uint32_t TMEM_COLS = 512;            // two FP32 accumulators of 128 lanes x 256 columns
-constexpr int THREADS = 192;                       // warp 0 TMA, warp 1 MMA, warps 2..5 epilogue
-constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+constexpr int XW = 16;                             // expander warps 2 .. 2 + XW - 1
+constexpr int THREADS = 64 + 32 * XW;              // warp 0 TMA, warp 1 MMA, warps 2.. expand (2..5: epilogue)
+constexpr int SB = 3;                              // stages of the packed-bit ring
+constexpr uint32_t BITS_ROW = BK / 8;              // 16 bytes of bits per row and K step
+constexpr uint32_t BITS_STAGE = (2 * BM + BN) * BITS_ROW;  // 8 KiB: rows of A0, A1, B
+constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + (size_t)SB * BITS_STAGE + 1024 /*align*/ + 256;
 constexpr uint32_t SPIN_LIMIT = 1u << 26;          // bounded waits (tens of ms per wait)
 
 struct Tile {
@@ -112,15 +116,37 @@ __device__ __forceinline__ void umma_commit(uint32_t bar) {
                  : "memory");
 }
 
+// The low four bits of v to four bytes, byte j = 0x38 (1.0 in e4m3) iff bit j
+// is set: the multiply by 1 + 2^7 + 2^14 + 2^21 copies the nibble to offsets
+// 0, 7, 14, 21 (disjoint bit ranges, so no carries), which puts bit j at the
+// low bit of byte j; the mask keeps those four bits.
+__device__ __forceinline__ uint32_t spread4(uint32_t v) {
+    return (((v & 15u) * 0x00204081u) & 0x01010101u) * 0x38u;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// One CTA per 256 x 256 block (two 128 x 256 tiles sharing B) over one K
+// range.  The operands stay packed in HBM (one bit per transaction): warp 0
+// loads the K step's bits of the 512 rows (8 KiB) with TMA into a 3-stage
+// ring; eight expander warps turn them into e4m3 {0, 1} bytes in the
+// 128-byte-swizzled layout the MMA reads (64 KiB per step, 3-stage ring) and
+// hand each stage to the MMA warp after a proxy fence; warp 1 issues the
+// tcgen05 MMAs; warps 2..5 then read the accumulators.
 __global__ void __launch_bounds__(THREADS, 1)
 k_dense_mmt(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
             const Tile *__restrict__ tiles, uint32_t ksplit, uint32_t kblocks, uint32_t n,
             uint32_t *__restrict__ C, int *__restrict__ err) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
-    // bars[0..STAGES): full, bars[STAGES..2*STAGES): empty, bars[2*STAGES]: accumulator ready
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 1);
+    uint8_t *bits = smem + STAGES * STAGE_BYTES;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(bits + SB * BITS_STAGE);
+    // bars: [0, SB) bits full (TMA), [SB, 2 SB) bits empty (expanders), [2 SB, 2 SB + S) bytes full
+    // (expanders), [2 SB + S, 2 SB + 2 S) bytes empty (MMA commit), [2 SB + 2 S] accumulators ready
+    constexpr int BF = 0, BE = SB, YF = 2 * SB, YE = 2 * SB + STAGES, ACC = 2 * SB + 2 * STAGES;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + ACC + 1);
     __shared__ volatile int s_abort;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -132,7 +158,8 @@ k_dense_mmt(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 
     if (threadIdx.x == 0) {
         s_abort = 0;
-        for (int i = 0; i < 2 * STAGES + 1; i++) mbar_init(smem_addr(&bars[i]), 1);
+        for (int i = 0; i <= ACC; i++)
+            mbar_init(smem_addr(&bars[i]), (i >= BE && i < BE + SB) || (i >= YF && i < YF + STAGES) ? XW : 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -146,27 +173,35 @@ k_dense_mmt(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 0 && lane == 0) {
-        // TMA producer
-        for (uint32_t it = 0; it < nk && !s_abort; it++) {
-            const uint32_t st = it % STAGES, round = it / STAGES;
-            if (round > 0 && !mbar_wait(smem_addr(&bars[STAGES + st]), (round - 1) & 1)) {
+        // TMA producer of the packed bits
+        uint32_t it = 0;
+        for (; it < nk && !s_abort; it++) {
+            const uint32_t sb = it % SB, ph = it / SB;
+            if (ph > 0 && !mbar_wait(smem_addr(&bars[BE + sb]), (ph - 1) & 1)) {
                 atomicExch(err, 1);
                 s_abort = 1;
                 break;
             }
-            const uint32_t full = smem_addr(&bars[st]);
-            uint8_t *sa = smem + st * STAGE_BYTES;
-            mbar_expect_tx(full, STAGE_BYTES);  // rows past the matrix are zero-filled and counted
-            const int kx = (int)((kb0 + it) * BK);
-            tma_load_2d(smem_addr(sa), &tmA, full, kx, (int)(2 * tile.bp * BM));
-            tma_load_2d(smem_addr(sa + A_BYTES), &tmA, full, kx, (int)((2 * tile.bp + 1) * BM));
-            tma_load_2d(smem_addr(sa + 2 * A_BYTES), &tmB, full, kx, (int)(tile.bj * BN));
+            const uint32_t full = smem_addr(&bars[BF + sb]);
+            uint8_t *dst = bits + sb * BITS_STAGE;
+            mbar_expect_tx(full, BITS_STAGE);  // rows past the matrix are zero-filled and counted
+            const int kx = (int)((kb0 + it) * BITS_ROW);
+            tma_load_2d(smem_addr(dst), &tmA, full, kx, (int)(2 * tile.bp * BM));
+            tma_load_2d(smem_addr(dst + BM * BITS_ROW), &tmA, full, kx, (int)((2 * tile.bp + 1) * BM));
+            tma_load_2d(smem_addr(dst + 2 * BM * BITS_ROW), &tmB, full, kx, (int)(tile.bj * BN));
+        }
+        if (s_abort) {
+            // wait (bounded) for the last load issued into every bits stage
+            for (uint32_t sb = 0; sb < (uint32_t)SB && sb < it; sb++) {
+                const uint32_t last = sb + SB * ((it - 1 - sb) / SB);
+                mbar_wait(smem_addr(&bars[BF + sb]), (last / SB) & 1);
+            }
         }
     } else if (warp == 1 && lane == 0) {
         // MMA issuer
         for (uint32_t it = 0; it < nk; it++) {
-            const uint32_t st = it % STAGES, round = it / STAGES;
-            if (s_abort || !mbar_wait(smem_addr(&bars[st]), round & 1)) {
+            const uint32_t st = it % STAGES;
+            if (s_abort || !mbar_wait(smem_addr(&bars[YF + st]), (it / STAGES) & 1)) {
                 atomicExch(err, 1);
                 s_abort = 1;
                 break;
@@ -181,57 +216,86 @@ k_dense_mmt(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                 umma_e4m3(tmem, da0 + (uint64_t)(k * 2), db + (uint64_t)(k * 2), acc);
                 umma_e4m3(tmem + (uint32_t)BN, da1 + (uint64_t)(k * 2), db + (uint64_t)(k * 2), acc);
             }
-            umma_commit(smem_addr(&bars[STAGES + st]));  // frees the stage when the MMAs have read it
+            umma_commit(smem_addr(&bars[YE + st]));  // frees the byte stage when the MMAs have read it
         }
-        umma_commit(smem_addr(&bars[2 * STAGES]));  // accumulator ready (or nothing issued)
+        umma_commit(smem_addr(&bars[ACC]));  // accumulators ready (or nothing issued)
     } else if (warp >= 2) {
-        // epilogue: TMEM lanes 32*(warp % 4) .. +31 hold tile rows of that quarter
-        const uint32_t q = warp & 3;
-        bool ready = false;
-        for (int rep = 0; rep < 16 && !ready; rep++) ready = mbar_wait(smem_addr(&bars[2 * STAGES]), 0);
-        if (!ready) {
-            atomicExch(err, 1);
-            s_abort = 1;
-        } else if (!s_abort && nk > 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint64_t nn = n;
-#pragma unroll 1
-            for (int h = 0; h < 2; h++) {
-            const uint32_t gi = (2 * tile.bp + h) * BM + q * 32 + lane;
-#pragma unroll 1
-            for (int c0 = 0; c0 < BN; c0 += 32) {
-                uint32_t v[32];
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-                    "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                      "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-                      "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
-                      "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
-                      "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-                    : "r"(tmem + ((q * 32u) << 16) + (uint32_t)(h * BN + c0)));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                if (gi < n) {
+        // expanders: thread t owns rows t, t + 32 XW, .. of the 512 rows (A0 0..127, A1 128..255,
+        // B 256..511); row r of the byte stage starts at r * 128, 16-byte chunk c at c ^ (r & 7)
+        const uint32_t t = (uint32_t)threadIdx.x - 64;
+        for (uint32_t it = 0; it < nk; it++) {
+            const uint32_t sb = it % SB, st = it % STAGES;
+            bool ok = !s_abort && mbar_wait(smem_addr(&bars[BF + sb]), (it / SB) & 1);
+            if (ok && it >= (uint32_t)STAGES) ok = mbar_wait(smem_addr(&bars[YE + st]), ((it / STAGES) - 1) & 1);
+            if (!ok) {
+                atomicExch(err, 1);
+                s_abort = 1;
+                break;
+            }
+            const uint8_t *src = bits + sb * BITS_STAGE;
+            uint8_t *dst = smem + st * STAGE_BYTES;
 #pragma unroll
-                    for (int c = 0; c < 32; c++) {
-                        const uint32_t gj = tile.bj * BN + c0 + c;
-                        const uint32_t cnt = __float2uint_rn(__uint_as_float(v[c]));
-                        if (gi < gj && gj < n && cnt)
-                            atomicAdd(&C[(uint64_t)gi * nn - (uint64_t)gi * (gi + 1) / 2 + (gj - gi - 1)], cnt);
+            for (uint32_t r = t; r < 2 * BM + BN; r += 32 * XW) {
+                const uint4 w = *reinterpret_cast<const uint4 *>(src + r * BITS_ROW);
+                const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+                uint8_t *row = dst + r * 128u;
+#pragma unroll
+                for (int c = 0; c < 8; c++) {
+                    const uint32_t h = ws[c >> 1] >> (16 * (c & 1));
+                    const uint4 o = make_uint4(spread4(h), spread4(h >> 4), spread4(h >> 8), spread4(h >> 12));
+                    *reinterpret_cast<uint4 *>(row + ((((uint32_t)c) ^ (r & 7u)) << 4)) = o;
+                }
+            }
+            // generic-proxy writes become visible to the tensor core's reads
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(smem_addr(&bars[YF + st]));
+                mbar_arrive(smem_addr(&bars[BE + sb]));
+            }
+        }
+        if (warp < 6) {
+            // epilogue: TMEM lanes 32*(warp % 4) .. +31 hold tile rows of that quarter
+            const uint32_t q = warp & 3;
+            bool ready = false;
+            for (int rep = 0; rep < 16 && !ready; rep++) ready = mbar_wait(smem_addr(&bars[ACC]), 0);
+            if (!ready) {
+                atomicExch(err, 1);
+                s_abort = 1;
+            } else if (!s_abort && nk > 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint64_t nn = n;
+#pragma unroll 1
+                for (int h = 0; h < 2; h++) {
+                    const uint32_t gi = (2 * tile.bp + h) * BM + q * 32 + lane;
+#pragma unroll 1
+                    for (int c0 = 0; c0 < BN; c0 += 32) {
+                        uint32_t v[32];
+                        asm volatile(
+                            "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                            "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                              "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+                              "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
+                              "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+                              "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
+                              "=r"(v[31])
+                            : "r"(tmem + ((q * 32u) << 16) + (uint32_t)(h * BN + c0)));
+                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                        if (gi < n) {
+#pragma unroll
+                            for (int c = 0; c < 32; c++) {
+                                const uint32_t gj = tile.bj * BN + c0 + c;
+                                const uint32_t cnt = __float2uint_rn(__uint_as_float(v[c]));
+                                if (gi < gj && gj < n && cnt)
+                                    atomicAdd(&C[(uint64_t)gi * nn - (uint64_t)gi * (gi + 1) / 2 + (gj - gi - 1)],
+                                              cnt);
+                            }
+                        }
                     }
                 }
             }
-            }
-        }
-    }
-    // drain: the producer's copies complete on the full barriers; with an abort,
-    // wait (bounded) for every stage that was armed but not consumed
-    __syncthreads();
-    if (s_abort && threadIdx.x == 0) {
-        for (uint32_t st = 0; st < (uint32_t)STAGES && st < nk; st++) {
-            const uint32_t uses = (nk - st + STAGES - 1) / STAGES;  // phases this stage went through
-            mbar_wait(smem_addr(&bars[st]), (uses - 1) & 1);
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -242,9 +306,9 @@ k_dense_mmt(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     }
 }
 
-// Scatter the tidlists into the zeroed e4m3 bitmap (1.0 = 0x38).
+// Scatter the tidlists into the zeroed bit matrix (row i, bit x = transaction x).
 __global__ void k_bitmap(const uint64_t *__restrict__ off, const uint32_t *__restrict__ tids, uint32_t n,
-                         uint32_t m, uint64_t ld, uint8_t *__restrict__ M, int *__restrict__ err) {
+                         uint32_t m, uint64_t ldw, uint32_t *__restrict__ M, int *__restrict__ err) {
     const uint32_t i = blockIdx.y;
     if (i >= n) return;
     const uint64_t b = off[i], e = off[i + 1];
@@ -255,7 +319,7 @@ __global__ void k_bitmap(const uint64_t *__restrict__ off, const uint32_t *__res
             atomicExch(err, 2);
             continue;
         }
-        M[(uint64_t)i * ld + x] = 0x38;
+        atomicOr(&M[(uint64_t)i * ldw + (x >> 5)], 1u << (x & 31));
     }
 }
 
@@ -277,15 +341,16 @@ static EncodeTiledFn encode_fn() {
     return fn;
 }
 
-static CUtensorMap make_map(void *base, uint64_t rows, uint64_t cols_elems, uint32_t box_rows) {
+// Packed bit rows viewed as bytes: box of BITS_ROW bytes (one K step) x box_rows rows.
+static CUtensorMap make_map(void *base, uint64_t rows, uint64_t row_bytes, uint32_t box_rows) {
     CUtensorMap map;
     std::memset(&map, 0, sizeof(map));
-    cuuint64_t dims[2] = {cols_elems, rows};
-    cuuint64_t strides[1] = {cols_elems};
-    cuuint32_t box[2] = {(cuuint32_t)BK, box_rows};
+    cuuint64_t dims[2] = {row_bytes, rows};
+    cuuint64_t strides[1] = {row_bytes};
+    cuuint32_t box[2] = {(cuuint32_t)BITS_ROW, box_rows};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = encode_fn()(&map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, base, dims, strides, box, estr,
-                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     BM_REQUIRE(r == CUDA_SUCCESS, BATMAP_ERR_CUDA, "cuTensorMapEncodeTiled failed");
     return map;
@@ -295,7 +360,7 @@ static CUtensorMap make_map(void *base, uint64_t rows, uint64_t cols_elems, uint
 
 // Workspace kept across calls (bitmap, supports, tile list, scratch).
 struct DenseWork {
-    DevBuf<uint8_t> bitmap;
+    DevBuf<uint32_t> bitmap;  // packed bit rows, ld bits each
     DevBuf<uint32_t> C;
     DevBuf<dense::Tile> tiles;
     DevBuf<int> err;
@@ -327,7 +392,8 @@ void run_dense(uint32_t m, uint32_t n, const uint64_t *d_off, const uint32_t *d_
     W.ev.create();
     W.ev.record(0, st);
     const uint64_t npairs = (uint64_t)n * (n > 0 ? n - 1 : 0) / 2;
-    const uint64_t ld = (m + BK - 1) / BK * BK;  // padded row length (elements)
+    const uint64_t ld = (m + BK - 1) / BK * BK;  // padded row length (bits)
+    const uint64_t ldw = ld / 32;                 // 32-bit words per row
     const uint64_t nrows = std::max<uint64_t>(n, 1);
     uint32_t *C = d_full;
     if (!C) {
@@ -336,11 +402,11 @@ void run_dense(uint32_t m, uint32_t n, const uint64_t *d_off, const uint32_t *d_
     }
     W.err.ensure(1);
     BM_CUDA(cudaMemsetAsync(W.err.p, 0, sizeof(int), st));
-    W.bitmap.ensure(nrows * ld);
-    BM_CUDA(cudaMemsetAsync(W.bitmap.p, 0, nrows * ld, st));
+    W.bitmap.ensure(nrows * ldw);
+    BM_CUDA(cudaMemsetAsync(W.bitmap.p, 0, nrows * ldw * 4, st));
     if (n) {
         dim3 grid((unsigned)std::min<uint64_t>((m + 255) / 256, 64), n);
-        k_bitmap<<<grid, 256, 0, st>>>(d_off, d_tids, n, m, ld, W.bitmap.p, W.err.p);
+        k_bitmap<<<grid, 256, 0, st>>>(d_off, d_tids, n, m, ldw, W.bitmap.p, W.err.p);
         BM_CHECK_LAUNCH();
     }
     W.ev.record(1, st);
@@ -356,12 +422,24 @@ void run_dense(uint32_t m, uint32_t n, const uint64_t *d_off, const uint32_t *d_
         int dev = 0, nsm = 0;
         BM_CUDA(cudaGetDevice(&dev));
         BM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-        uint32_t ksplit = std::max<uint32_t>(1, (uint32_t)((2u * nsm + tl.size() - 1) / tl.size()));
-        ksplit = std::min<uint32_t>(ksplit, std::max<uint32_t>(1, kblocks / 8));
+        // K split: one CTA per SM at a time, so choose the split whose CTA count fills its last
+        // wave best (whole waves of equal CTAs), preferring fewer splits; each K range keeps
+        // at least 64 K steps
+        const uint32_t ntiles = (uint32_t)tl.size();
+        uint32_t ksplit = 1;
+        double best = -1.0;
+        for (uint32_t k = 1; k <= 16 && (k == 1 || 64u * k <= kblocks); k++) {
+            const uint64_t u = (uint64_t)ntiles * k, waves = (u + nsm - 1) / nsm;
+            const double score = (double)u / (double)(waves * (uint64_t)nsm) - 0.01 * k;
+            if (score > best) {
+                best = score;
+                ksplit = k;
+            }
+        }
         W.tiles.ensure(tl.size());
         BM_CUDA(cudaMemcpyAsync(W.tiles.p, tl.data(), tl.size() * sizeof(Tile), cudaMemcpyHostToDevice, st));
-        CUtensorMap mA = make_map(W.bitmap.p, nrows, ld, BM);
-        CUtensorMap mB = make_map(W.bitmap.p, nrows, ld, BN);
+        CUtensorMap mA = make_map(W.bitmap.p, nrows, ld / 8, BM);
+        CUtensorMap mB = make_map(W.bitmap.p, nrows, ld / 8, BN);
         static bool attr = false;
         if (!attr) {
             BM_CUDA(cudaFuncSetAttribute(k_dense_mmt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM));
