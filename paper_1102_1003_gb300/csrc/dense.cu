@@ -309,17 +309,17 @@ k_dense_mmt(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 // Scatter the tidlists into the zeroed bit matrix (row i, bit x = transaction x).
 __global__ void k_bitmap(const uint64_t *__restrict__ off, const uint32_t *__restrict__ tids, uint32_t n,
                          uint32_t m, uint64_t ldw, uint32_t *__restrict__ M, int *__restrict__ err) {
-    const uint32_t i = blockIdx.y;
-    if (i >= n) return;
-    const uint64_t b = off[i], e = off[i + 1];
-    for (uint64_t k = b + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < e;
-         k += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t x = tids[k];
-        if (x >= m) {
-            atomicExch(err, 2);
-            continue;
+    for (uint32_t i = blockIdx.y; i < n; i += gridDim.y) {
+        const uint64_t b = off[i], e = off[i + 1];
+        for (uint64_t k = b + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < e;
+             k += (uint64_t)gridDim.x * blockDim.x) {
+            const uint32_t x = tids[k];
+            if (x >= m) {
+                atomicExch(err, 2);
+                continue;
+            }
+            atomicOr(&M[(uint64_t)i * ldw + (x >> 5)], 1u << (x & 31));
         }
-        atomicOr(&M[(uint64_t)i * ldw + (x >> 5)], 1u << (x & 31));
     }
 }
 
@@ -405,7 +405,7 @@ void run_dense(uint32_t m, uint32_t n, const uint64_t *d_off, const uint32_t *d_
     W.bitmap.ensure(nrows * ldw);
     BM_CUDA(cudaMemsetAsync(W.bitmap.p, 0, nrows * ldw * 4, st));
     if (n) {
-        dim3 grid((unsigned)std::min<uint64_t>((m + 255) / 256, 64), n);
+        dim3 grid((unsigned)std::min<uint64_t>((m + 255) / 256, 64), std::min<uint32_t>(n, 65535u));
         k_bitmap<<<grid, 256, 0, st>>>(d_off, d_tids, n, m, ldw, W.bitmap.p, W.err.p);
         BM_CHECK_LAUNCH();
     }
