@@ -389,17 +389,18 @@ batmap_status batmap_serve(const batmap_pool *pool, const uint32_t *h_qoff, cons
 /*
  * Dense-bitmap comparison path (Sec. I-B: the bitmap vertical representation,
  * m*n bits, where a support is AND + popcount).  Builds the item x transaction
- * bitmap as e4m3 {0, 1} bytes and computes all supports as the dense
- * contraction M M^T on the tensor cores (tcgen05 kind::f8f6f4, FP32
- * accumulation in tensor memory, exact because every product is 0 or 1 and
- * every partial sum an integer below 2^24), then the same threshold
- * compaction as pair_support_all.
+ * bit matrix (packed, one bit per pair) and computes all supports as the dense
+ * contraction M M^T on the tensor cores: each K step's bits are expanded to
+ * e4m3 {0, 1} bytes in shared memory and multiplied with tcgen05
+ * kind::f8f6f4 (FP32 accumulation in tensor memory, exact because every
+ * product is 0 or 1 and every partial sum an integer below 2^24), then the
+ * same threshold compaction as pair_support_all.
  *   m, n, d_offsets, d_tids : CSR tidlists as in batmap_build (1 <= m <= 2^24).
  *   s, d_pairs, cap, n_out, d_full : as in pair_support_all.
  *   timing  : optional host struct; build_ms = bitmap build, compare_ms = the
  *             tensor-core kernel, compact_ms = compaction.
- * The bitmap (n x ceil(m/128)*128 bytes) and scratch are cached inside
- * the library between calls.  Synchronises the stream.
+ * The bit matrix (n rows of ceil(m/128)*128 bits) and scratch are cached
+ * inside the library between calls.  Synchronises the stream.
  */
 batmap_status pair_support_dense(uint32_t m, uint32_t n, const uint64_t *d_offsets, const uint32_t *d_tids,
                                  uint32_t s, uint32_t *d_pairs, uint64_t cap, uint64_t *n_out,
