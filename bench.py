@@ -361,7 +361,11 @@ def run_batch(args):
     import oracle
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
-    specs = datagen.batch_specs(args.instances, 1000)
+    if args.batch_small:
+        # many small instances, where per-call launches and synchronisations dominate
+        specs = datagen.batch_specs(args.instances, 5000, m_range=(1e3, 1e5), n_range=(50, 400))
+    else:
+        specs = datagen.batch_specs(args.instances, 1000)
     t0 = time.perf_counter()
     insts = datagen.batch_instances(specs, workers=os.cpu_count() or 8)
     gen_s = time.perf_counter() - t0
@@ -423,7 +427,8 @@ def run_batch(args):
     line = {"metric": METRIC, "workload": "batch", "unit": UNIT, "value": results["batched"]["value"],
             "ms_per_step": results["batched"]["ms_per_step"], "plain": results["plain"],
             "speedup_batched_over_plain": results["batched"]["value"] / results["plain"]["value"],
-            "config": {"instances": len(insts), "pairs": npairs, "tids": int(sum(i.tids.size for i in insts)),
+            "config": {"instances": len(insts), "small": bool(args.batch_small), "pairs": npairs,
+                       "tids": int(sum(i.tids.size for i in insts)),
                        "m_range": [min(i.m for i in insts), max(i.m for i in insts)],
                        "n_range": [min(i.n for i in insts), max(i.n for i in insts)],
                        "autotuned": eff is not None},
@@ -771,6 +776,8 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOAD_DESC) + ["serve", "batch", "nsweep", "cross", "triples"], default="zipf_m1m_n2000")
     ap.add_argument("--nsweep", type=int, nargs="+", default=[1000, 2000, 4000, 8000, 16000, 32000, 64000])
     ap.add_argument("--instances", type=int, default=64, help="instances (batch workload)")
+    ap.add_argument("--batch-small", action="store_true",
+                    help="batch workload of small instances (m in [1e3, 1e5], n in [50, 400])")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--pool-sets", type=int, default=100_000, help="serving pool size (serve workload)")
     ap.add_argument("--queries", type=int, default=200_000, help="queries per serving run (serve workload)")
