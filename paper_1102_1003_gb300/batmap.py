@@ -398,11 +398,11 @@ def pair_support_dense(m: int, offsets, tids, s: int, pairs=None, full=None, str
 
 def batmap_autotune(sets, stream=None):
     """Measure every tile shape on these sets, adopt the result for scheduling and
-    reschedule them; returns the relative throughput per shape (1..13)."""
+    reschedule them; returns the relative throughput per shape (1..16)."""
     L = load_library()
     k = len(sets)
     handles = (ctypes.c_void_p * k)(*[b.handle for b in sets])
-    eff = (ctypes.c_double * 13)()
+    eff = (ctypes.c_double * 16)()
     _check(L.batmap_autotune(handles, k, eff, _stream_handle(stream)))
     return list(eff)
 

@@ -26,7 +26,7 @@ struct BatchPlan {
     DevBuf<WorkUnit> d_units;
     DevBuf<uint32_t> d_counter;
     DevBuf<uint64_t> d_totals;
-    uint32_t nunits = 0;
+    uint32_t nunits = 0, nmain = 0;
     cudaStream_t stream = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -60,9 +60,8 @@ static void enqueue_batch(BatchPlan *P, batmap_set *const *sets, const uint32_t 
         const uint64_t np = sets[q]->npairs();
         if (np) BM_CUDA(cudaMemsetAsync(P->C[q], 0, np * sizeof(uint32_t), st));
     }
-    BM_CUDA(cudaMemsetAsync(P->d_counter.p, 0, sizeof(uint32_t), st));
-    launch_compare(P->d_views.p, P->d_units.p, P->nunits, P->d_counter.p,
-                   std::min<uint32_t>(P->nunits, (uint32_t)device_sms()), st);
+    BM_CUDA(cudaMemsetAsync(P->d_counter.p, 0, 2 * sizeof(uint32_t), st));
+    launch_compare(P->d_views.p, P->d_units.p, P->nunits, P->nmain, P->d_counter.p, st);
     for (uint32_t q = 0; q < k; q++)
         enqueue_correct_compact(sets[q], P->C[q], s[q], outs[q].d_pairs, outs[q].cap, P->d_totals.p + q, st);
 }
@@ -93,9 +92,10 @@ static BatchPlan *make_plan(batmap_set *const *sets, const uint32_t *s, uint32_t
     }
     sort_units(&units);
     P->nunits = (uint32_t)units.size();
+    P->nmain = main_units(units);
     P->d_views.alloc(k);
     P->d_units.alloc(units.size());
-    P->d_counter.alloc(1);
+    P->d_counter.alloc(2);
     P->d_totals.alloc(k);
     BM_CUDA(cudaMemcpyAsync(P->d_views.p, views.data(), k * sizeof(InstView), cudaMemcpyHostToDevice, st));
     if (!units.empty())
@@ -194,7 +194,7 @@ void autotune(batmap_set *const *sets, uint32_t k, double *eff_out, cudaStream_t
                                  S->d_order.p, S->d_C.p, S->n, S->n_a});
     }
     DevBuf<InstView> d_views(views.size());
-    DevBuf<uint32_t> d_counter(1);
+    DevBuf<uint32_t> d_counter(2);
     BM_CUDA(cudaMemcpyAsync(d_views.p, views.data(), views.size() * sizeof(InstView), cudaMemcpyHostToDevice, st));
     PhaseEvents ev;
     ev.create();
@@ -217,10 +217,9 @@ void autotune(batmap_set *const *sets, uint32_t k, double *eff_out, cudaStream_t
         DevBuf<WorkUnit> d_units(units.size());
         if (!units.empty())
             BM_CUDA(cudaMemcpyAsync(d_units.p, units.data(), units.size() * sizeof(WorkUnit), cudaMemcpyHostToDevice, st));
-        BM_CUDA(cudaMemsetAsync(d_counter.p, 0, sizeof(uint32_t), st));
+        BM_CUDA(cudaMemsetAsync(d_counter.p, 0, 2 * sizeof(uint32_t), st));
         ev.record(0, st);
-        launch_compare(d_views.p, d_units.p, (uint32_t)units.size(), d_counter.p,
-                       std::min<uint32_t>((uint32_t)units.size(), (uint32_t)device_sms()), st);
+        launch_compare(d_views.p, d_units.p, (uint32_t)units.size(), main_units(units), d_counter.p, st);
         ev.record(1, st);
         BM_CUDA(cudaStreamSynchronize(st));
         const double ms = ev.ms(0, 1);

@@ -53,12 +53,11 @@ static batmap_status guarded(F &&f) {
 void enqueue_compare(batmap_set *S, uint32_t *C, const InstView *d_view, cudaStream_t st) {
     const uint64_t npairs = S->npairs();
     if (npairs) BM_CUDA(cudaMemsetAsync(C, 0, npairs * sizeof(uint32_t), st));
-    S->d_counters.ensure(1);
-    BM_CUDA(cudaMemsetAsync(S->d_counters.p, 0, sizeof(uint32_t), st));
+    S->d_counters.ensure(2);
+    BM_CUDA(cudaMemsetAsync(S->d_counters.p, 0, 2 * sizeof(uint32_t), st));
     const uint32_t count = (uint32_t)S->units.size();
     S->pairs_ev.record(1, st);
-    launch_compare(d_view, S->d_units.p, count, S->d_counters.p,
-                   std::min<uint32_t>(count, (uint32_t)device_sms()), st);
+    launch_compare(d_view, S->d_units.p, count, main_units(S->units), S->d_counters.p, st);
     S->pairs_ev.record(2, st);
 }
 
@@ -94,7 +93,7 @@ static batmap_status build_any(const batmap_params *p, uint32_t m, uint32_t n, u
         BM_REQUIRE(P.load_num >= 1 && P.load_den >= 1 && P.load_num <= 16 * P.load_den,
                    BATMAP_ERR_ARG, "load factor must be in [1/load_den, 16]");
         BM_REQUIRE(P.min_shift >= 7 && P.min_shift <= 24, BATMAP_ERR_ARG, "min_shift must be in [7, 24]");
-        BM_REQUIRE(P.tile <= NUM_SHAPES, BATMAP_ERR_ARG, "tile must be 0..13");
+        BM_REQUIRE(P.tile <= NUM_SHAPES, BATMAP_ERR_ARG, "tile must be 0..16");
         BM_REQUIRE(P.max_loop >= 1 && P.max_loop <= (1u << 20), BATMAP_ERR_ARG, "max_loop out of range");
         batmap_set *S = new batmap_set();
         S->params = P;

@@ -31,8 +31,8 @@
 
 namespace bm {
 
-// Shapes 1..6 stage tiles through shared memory (cp.async ring); shapes
-// 7..13 stream operands from global memory into registers.  The efficiency
+// Shapes 1..6 and 14..16 stage tiles through shared memory (cp.async ring);
+// shapes 7..13 stream operands from global memory into registers.  The efficiency
 // column is the prior relative throughput per padded word pair used when no
 // autotuned table is available: on the m = 10^6, n = 2,000 Zipf workload, the
 // rate each shape reaches on the width classes it serves there (shapes 1, 2,
@@ -46,6 +46,10 @@ const ShapeDesc SHAPES[NUM_SHAPES] = {
     {9, 512, 32, 8, 4, 0, 0.834},    {10, 1024, 16, 8, 4, 0, 0.811},
     {11, 2048, 8, 8, 4, 0, 0.827},   {12, 2048, 4, 4, 4, 0, 0.689},
     {13, 1024, 12, 12, 4, 0, 0.912},
+    // one column per thread, few rows: for width classes of small instances
+    // (priors from batmap_autotune on 1,024 instances with m in [1e3, 1e5], n in [50, 400])
+    {14, 256, 8, 1, 32, 3, 0.545},   {15, 128, 16, 1, 32, 3, 0.599},
+    {16, 64, 32, 1, 32, 3, 0.619},
 };
 
 int device_sms() {
@@ -426,6 +430,12 @@ __device__ __forceinline__ void process_unit_direct(uint4 *smem, const InstView 
     X(4, 256, 1, 8, 8, 2)         \
     X(5, 256, 1, 4, 8, 2)
 
+// One column per thread (shapes 14..16), staged like shapes 1..6.
+#define BM_SMALL_LIST(X)          \
+    X(13, 32, 8, 1, 32, 3)        \
+    X(14, 16, 16, 1, 32, 3)       \
+    X(15, 8, 32, 1, 32, 3)
+
 #define BM_DIRECT_LIST(X)      \
     X(6, 16, 16, 8, 8, false)    \
     X(7, 32, 8, 8, 8, false)     \
@@ -438,6 +448,7 @@ __device__ __forceinline__ void process_unit_direct(uint4 *smem, const InstView 
 size_t compare_smem_bytes(uint32_t shape_idx) {
 #define X(i, a, b, c, d, e) if (shape_idx == i) return Tile<a, b, c, d, e>::SMEM;
     BM_SHAPE_LIST(X)
+    BM_SMALL_LIST(X)
 #undef X
     return 0;
 }
@@ -447,7 +458,8 @@ static size_t max_smem_bytes() {
 #define X(i, a, b, c, d, e) m = std::max(m, DirectTile<a, b, c, d, e>::SMEM);
     BM_DIRECT_LIST(X)
 #undef X
-    for (uint32_t s = 0; s < NUM_SHAPES; s++) m = std::max(m, compare_smem_bytes(s));
+    for (uint32_t s = 0; s < NUM_SHAPES; s++)
+        if (!small_shape(s)) m = std::max(m, compare_smem_bytes(s));
     return m;
 }
 
@@ -478,22 +490,63 @@ k_compare(const InstView *__restrict__ views, const WorkUnit *__restrict__ units
     }
 }
 
-static size_t g_compare_smem = 0;
+// The one-column-per-thread shapes run in a kernel of their own (after the
+// main one, on its own counter), so that they leave the register allocation
+// of the main shapes' loops untouched.
+__global__ void __launch_bounds__(256, 1)
+k_compare_small(const InstView *__restrict__ views, const WorkUnit *__restrict__ units, uint32_t count,
+                uint32_t *__restrict__ counter) {
+    extern __shared__ __align__(16) uint4 smem[];
+    __shared__ uint32_t s_unit;
+    for (;;) {
+        if (threadIdx.x == 0) s_unit = atomicAdd(counter, 1u);
+        __syncthreads();
+        const uint32_t u = s_unit;
+        __syncthreads();
+        if (u >= count) break;
+        const WorkUnit wu = units[u];
+        const InstView V = views[wu.inst];
+        switch (wu.shape & UNIT_SHAPE_MASK) {
+#define X(i, a, b, c, d, e) case i: process_unit<a, b, c, d, e>(smem, V, wu); break;
+            BM_SMALL_LIST(X)
+#undef X
+            default: break;
+        }
+    }
+}
+
+static size_t g_compare_smem = 0, g_small_smem = 0;
 
 void prepare_compare() {
     if (!g_compare_smem) {
         size_t smem = max_smem_bytes();
         BM_CUDA(cudaFuncSetAttribute(k_compare, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         g_compare_smem = smem;
+        size_t small = 0;
+#define X(i, a, b, c, d, e) small = std::max(small, Tile<a, b, c, d, e>::SMEM);
+        BM_SMALL_LIST(X)
+#undef X
+        BM_CUDA(cudaFuncSetAttribute(k_compare_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)small));
+        g_small_smem = small;
     }
 }
 
-void launch_compare(const InstView *d_views, const WorkUnit *d_units, uint32_t count, uint32_t *d_counter,
-                    uint32_t grid, cudaStream_t st) {
+bool small_shape(uint32_t shape) { return (shape & UNIT_SHAPE_MASK) >= 13; }
+
+void launch_compare(const InstView *d_views, const WorkUnit *d_units, uint32_t count, uint32_t nmain,
+                    uint32_t *d_counters, cudaStream_t st) {
     if (!count) return;
     prepare_compare();
-    k_compare<<<grid, 256, g_compare_smem, st>>>(d_views, d_units, count, d_counter);
-    BM_CHECK_LAUNCH();
+    const uint32_t sms = (uint32_t)device_sms();
+    if (nmain) {
+        k_compare<<<std::min(nmain, sms), 256, g_compare_smem, st>>>(d_views, d_units, nmain, d_counters);
+        BM_CHECK_LAUNCH();
+    }
+    if (count > nmain) {
+        k_compare_small<<<std::min(count - nmain, sms), 256, g_small_smem, st>>>(d_views, d_units + nmain,
+                                                                                count - nmain, d_counters + 1);
+        BM_CHECK_LAUNCH();
+    }
 }
 
 // ---- schedule ------------------------------------------------------------------
@@ -603,6 +656,13 @@ double unit_cost(const WorkUnit &u) {
 void sort_units(std::vector<WorkUnit> *units) {
     std::stable_sort(units->begin(), units->end(),
                      [](const WorkUnit &a, const WorkUnit &b) { return unit_cost(a) > unit_cost(b); });
+    std::stable_partition(units->begin(), units->end(), [](const WorkUnit &u) { return !small_shape(u.shape); });
+}
+
+uint32_t main_units(const std::vector<WorkUnit> &units) {
+    uint32_t k = 0;
+    while (k < units.size() && !small_shape(units[k].shape)) k++;
+    return k;
 }
 
 bool tuned_shape_eff(double *eff);  // batch.cu

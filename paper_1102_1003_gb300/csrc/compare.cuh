@@ -16,7 +16,7 @@ struct ShapeDesc {
     double eff;    // relative throughput per padded word-pair (scheduler prior)
 };
 
-constexpr int NUM_SHAPES = 13;
+constexpr int NUM_SHAPES = 16;
 extern const ShapeDesc SHAPES[NUM_SHAPES];
 
 // Number of SMs of the current device (cached).
@@ -31,15 +31,19 @@ void schedule_units(const batmap_set *S, uint32_t force_shape, const double *sha
                     double target_cost, std::vector<WorkUnit> *out);
 
 // Estimated cost of a unit (padded word-pairs / shape efficiency) and the
-// longest-first order used by every launch.
+// order used by every launch: units of the main shapes first, then those of
+// the one-column shapes 14..16 (small_shape), each part longest first.
 double unit_cost(const WorkUnit &u);
 void sort_units(std::vector<WorkUnit> *units);
+bool small_shape(uint32_t shape);
+uint32_t main_units(const std::vector<WorkUnit> &units);  // length of the first part
 
-// Launch the persistent compare kernel over `count` units at d_units (any
-// mix of shapes and instances), pulling work from d_counter (zeroed by the
-// caller).  One CTA per SM.
-void launch_compare(const InstView *d_views, const WorkUnit *d_units, uint32_t count,
-                    uint32_t *d_counter, uint32_t grid, cudaStream_t st);
+// Launch the persistent compare kernels over `count` units at d_units (any
+// mix of instances) ordered by sort_units, the first nmain of the main
+// shapes: one kernel per part, pulling work from d_counters[0] and
+// d_counters[1] (zeroed by the caller).  One CTA per SM.
+void launch_compare(const InstView *d_views, const WorkUnit *d_units, uint32_t count, uint32_t nmain,
+                    uint32_t *d_counters, cudaStream_t st);
 
 // Sets the kernel's shared-memory attribute (call before stream capture).
 void prepare_compare();

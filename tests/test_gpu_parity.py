@@ -65,7 +65,7 @@ def test_zipf_mixed_widths_exact_and_valid(seed):
     assert layout_errors(inst, bset, seed) == []
 
 
-@pytest.mark.parametrize("tile", list(range(1, 14)))
+@pytest.mark.parametrize("tile", list(range(1, 17)))
 def test_every_tile_shape_exact(tile):
     import paper_1102_1003_gb300 as pkg
     inst = datagen.zipf_tidlists(40_000, 333, 0.04, seed=7, s=30)
