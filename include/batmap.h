@@ -58,11 +58,11 @@ typedef int batmap_status;
  *       Must be >= 7 so that every BatMap is a multiple of 384 bytes.
  *       Default 7.
  *   tile : 0 lets the scheduler choose compare tile shapes per width class;
- *       1..13 forces one shape for every class (testing and autotuning).
+ *       1..16 forces one shape for every class (testing and autotuning).
  *   validate : nonzero checks that tids are strictly increasing and < m per
  *       item and that each permutation row is a bijection of [0, m); a
  *       violation returns BATMAP_ERR_ARG.  Default 1.
- *   shape_mask : bit s-1 allows compare tile shape s (1..13) when tile is 0;
+ *   shape_mask : bit s-1 allows compare tile shape s (1..16) when tile is 0;
  *       0 allows every shape.  Default 0.
  */
 typedef struct batmap_params {
@@ -260,7 +260,7 @@ batmap_status pair_support_host(const batmap_params *p, uint32_t m, uint32_t n,
  * batmap_build in the process, and all k sets are rescheduled with them (the
  * width class -> tile shape choice and the split of column words into work
  * units).
- *   shape_eff : optional host double[13], receives the relative throughputs.
+ *   shape_eff : optional host double[16], receives the relative throughputs.
  * Synchronises the stream.
  */
 batmap_status batmap_autotune(batmap_set *const *sets, uint32_t k, double *shape_eff, cudaStream_t stream);
