@@ -431,11 +431,14 @@ __global__ void k_check_ids(const uint32_t *ids, uint64_t count, uint32_t n, int
 //
 // The candidates of the frequent pair p = (a, b) are contiguous
 // (cand_off[p] .. cand_off[p+1]).  A work unit is up to GROUP of them: the
-// warp reads a's and b's words once per step and every c of the unit against
-// them.  Lanes read 16-byte chunks; a table block is r_0 >= 128 bytes, so the
-// four words of a chunk share one table (lanes may differ: the witness
-// requirement is selected per lane).
+// warp reads a's and b's chunks once and every c of the unit against them.
+// Lanes read 16-byte chunks; a table block is r_0 >= 128 bytes (8 chunks), so
+// a chunk lies in one table.  The warp takes the four tables one after the
+// other (chunk k of table t is q = 4 * 2^tq * (k >> tq) + t * 2^tq + (k mod
+// 2^tq), 2^tq chunks per table block), so the witness requirement is a
+// compile-time case of each pass.
 constexpr uint32_t GROUP = 8;
+constexpr uint32_t WG_TPB = 128;  // threads per block of k_witness_group
 
 __global__ void k_unit_counts(const uint64_t *cand_off, uint64_t np, uint64_t *ucnt) {
     for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < np;
@@ -451,12 +454,91 @@ __global__ void k_unit_fill(const uint64_t *cand_off, const uint64_t *uoff, uint
     }
 }
 
-__global__ void __launch_bounds__(256) k_witness_group(View V, const uint32_t *__restrict__ pairs,
+// What a and b leave to c in one word, per lane, for a slot of table T: the
+// tables u < T that neither a nor b misses.  None: c is free; exactly one,
+// v: c must miss v; two or more: no c makes T the witness.  This becomes an
+// expected byte pat (a's code; v in the top bits where constrained) under a
+// mask msk (msk7 = msk without bit 7) and a validity flag val (bit 7) for
+// lanes where a and b agree on a nonempty code and the rule can hold.  Bit 7
+// of x holds the high bit of the lane's missing table and bit 7 of x << 1 the
+// low bit.
+template <int T>
+__device__ __forceinline__ void pair_rule(uint32_t xa, uint32_t xb, uint32_t &pat, uint32_t &msk, uint32_t &msk7,
+                                          uint32_t &val) {
+    constexpr uint32_t C6 = 0x3F3F3F3Fu, H7 = 0x80808080u, L7 = 0x7E7E7E7Eu;
+    const uint32_t za = xa & C6;
+    // bit 7 of 2 e + 0x7E (e <= 0x3F per lane, no carry leaves a lane) is set iff e != 0
+    const uint32_t ne = ((xa ^ xb) & C6) * 2u + L7;  // codes differ
+    const uint32_t nz = za * 2u + L7;                // slot not empty
+    if (T == 0) {
+        pat = za;
+        msk = msk7 = C6;
+        val = nz & ~ne & H7;
+        return;
+    }
+    const uint32_t a2 = xa << 1, b2 = xb << 1;
+    const uint32_t u0 = (xa | a2) & (xb | b2) & H7;                     // neither misses table 0
+    const uint32_t u1 = T >= 2 ? (xa | ~a2) & (xb | ~b2) & H7 : 0u;     // neither misses table 1
+    const uint32_t u2 = T >= 3 ? (~xa | a2) & (~xb | b2) & H7 : 0u;     // neither misses table 2
+    const uint32_t two = (u0 & u1) | (u0 & u2) | (u1 & u2);
+    const uint32_t q7 = u0 | u1 | u2;
+    pat = za | (u1 >> 1) | u2;
+    msk7 = C6 | (q7 >> 1);
+    msk = msk7 | q7;
+    val = nz & ~ne & ~two & H7;
+}
+
+// One pass of a unit over the chunks of table T.
+template <int T>
+__device__ __forceinline__ void group_pass(const uint4 *__restrict__ bm4, uint32_t lane, uint32_t tq, uint32_t kmax,
+                                           uint64_t ca, uint32_t ma, uint64_t cb, uint32_t mb,
+                                           const uint64_t (&cc)[GROUP], const uint32_t (&mc)[GROUP],
+                                           const uint32_t (&klim)[GROUP], uint32_t (&cnt)[GROUP]) {
+    constexpr uint32_t C6 = 0x3F3F3F3Fu, K7 = 0x7F7F7F7Fu;
+    const uint32_t low = (1u << tq) - 1u;
+    for (uint32_t k = lane; k < kmax; k += 32) {
+        const uint32_t q = ((k & ~low) << 2) | ((uint32_t)T << tq) | (k & low);
+        const uint4 A = __ldg(&bm4[ca + (q & ma)]);
+        const uint4 Bv = __ldg(&bm4[cb + (q & mb)]);
+        // all of the unit's column chunks are requested before any is used
+        uint4 Cs[GROUP];
+#pragma unroll
+        for (uint32_t j = 0; j < GROUP; j++)
+            Cs[j] = k < klim[j] ? __ldg(&bm4[cc[j] + (q & mc[j])]) : make_uint4(0, 0, 0, 0);
+        const uint32_t xa[4] = {A.x, A.y, A.z, A.w}, xb[4] = {Bv.x, Bv.y, Bv.z, Bv.w};
+        uint32_t pat[4], msk[4], msk7[4], val[4];
+#pragma unroll
+        for (int w = 0; w < 4; w++) pair_rule<T>(xa[w], xb[w], pat[w], msk[w], msk7[w], val[w]);
+#pragma unroll
+        for (uint32_t j = 0; j < GROUP; j++) {
+            if (k >= klim[j]) continue;  // also skips the unit's unused slots (klim = 0)
+            const uint32_t xc[4] = {Cs[j].x, Cs[j].y, Cs[j].z, Cs[j].w};
+            uint32_t hits = 0;
+#pragma unroll
+            for (int w = 0; w < 4; w++) {
+                uint32_t ok;
+                if (T == 0) {
+                    // c is free: only the code has to agree
+                    ok = val[w] & ~(((xc[w] ^ xa[w]) & C6) + K7);
+                } else {
+                    // lane of d is zero iff c matches the expected byte under the mask;
+                    // bit 7 of d7 + 0x7F.. flags a nonzero lane of d7 (no carry leaves a lane)
+                    const uint32_t d = (xc[w] ^ pat[w]) & msk[w];
+                    const uint32_t d7 = (xc[w] ^ pat[w]) & msk7[w];
+                    ok = val[w] & ~((d7 + K7) | d);
+                }
+                hits = __dp4a(ok, 0x01010101u, hits);  // 128 per counted slot
+            }
+            cnt[j] += hits >> 7;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(WG_TPB) k_witness_group(View V, const uint32_t *__restrict__ pairs,
                                                        const uint64_t *__restrict__ cand_off,
                                                        const uint32_t *__restrict__ cand,
                                                        const uint2 *__restrict__ units, uint64_t nu,
                                                        uint32_t *__restrict__ sup) {
-    constexpr uint32_t C6 = 0x3F3F3F3Fu, B6 = 0x40404040u, H7 = 0x80808080u;
     const uint32_t lane = threadIdx.x & 31u;
     const uint4 *bm4 = reinterpret_cast<const uint4 *>(V.bm);
     const uint32_t tq = V.shift - 4;  // 16-byte chunks per table block = r_0 / 16 = 2^(s-4)
@@ -471,8 +553,8 @@ __global__ void __launch_bounds__(256) k_witness_group(View V, const uint32_t *_
         const uint64_t ca = V.base[a] >> 4, cb = V.base[b] >> 4;
         const uint32_t ma = ra / 4 - 1, mb = rb / 4 - 1;
         uint64_t cc[GROUP];
-        uint32_t mc[GROUP], lim[GROUP], cnt[GROUP];
-        uint32_t qmax = 0;
+        uint32_t mc[GROUP], klim[GROUP], cnt[GROUP];
+        uint32_t kmax = 0;
 #pragma unroll
         for (uint32_t j = 0; j < GROUP; j++) {
             cnt[j] = 0;
@@ -481,67 +563,18 @@ __global__ void __launch_bounds__(256) k_witness_group(View V, const uint32_t *_
                 const uint32_t rc = 1u << V.rlog[c];
                 cc[j] = V.base[c] >> 4;
                 mc[j] = rc / 4 - 1;
-                lim[j] = max(max(ra, rb), rc) / 4;  // chunks this triple runs over
+                klim[j] = max(max(ra, rb), rc) / 16;  // chunks of one table this triple runs over
             } else {
                 cc[j] = 0;
                 mc[j] = 0;
-                lim[j] = 0;
+                klim[j] = 0;
             }
-            qmax = max(qmax, lim[j]);
+            kmax = max(kmax, klim[j]);
         }
-        for (uint32_t q = lane; q < qmax; q += 32) {
-            // n_u (bit 7 of every lane): table u < t must be missed by some set
-            const uint32_t t = (q >> tq) & 3u;
-            const uint32_t n0 = t >= 1 ? H7 : 0u, n1 = t >= 2 ? H7 : 0u, n2 = t >= 3 ? H7 : 0u;
-            const uint4 A = __ldg(&bm4[ca + (q & ma)]);
-            const uint4 Bv = __ldg(&bm4[cb + (q & mb)]);
-            // all of the unit's column chunks are requested before any is used
-            uint4 Cs[GROUP];
-#pragma unroll
-            for (uint32_t j = 0; j < GROUP; j++)
-                Cs[j] = q < lim[j] ? __ldg(&bm4[cc[j] + (q & mc[j])]) : make_uint4(0, 0, 0, 0);
-            const uint32_t xa[4] = {A.x, A.y, A.z, A.w}, xb[4] = {Bv.x, Bv.y, Bv.z, Bv.w};
-            // What a and b leave to c, per lane: the tables u < t that neither
-            // a nor b misses (u_0, u_1, u_2).  None: c is free; exactly one v:
-            // c must miss v; two or more: no c can make t the witness.  This
-            // becomes an expected byte pat (a's code, v in the top bits where
-            // constrained) under a mask msk, and a validity bit (bit 7) for
-            // lanes where a and b agree on a nonempty code and the rule can hold.
-            // The flags live in bit 7 of each lane, where x holds the high bit
-            // of its missing table and x << 1 the low bit.
-            uint32_t pat[4], msk[4], msk7[4], val[4];
-#pragma unroll
-            for (int k = 0; k < 4; k++) {
-                const uint32_t a2 = xa[k] << 1, b2 = xb[k] << 1;
-                const uint32_t u0 = n0 & (xa[k] | a2) & (xb[k] | b2);    // neither misses table 0
-                const uint32_t u1 = n1 & (xa[k] | ~a2) & (xb[k] | ~b2);  // neither misses table 1
-                const uint32_t u2 = n2 & (~xa[k] | a2) & (~xb[k] | b2);  // neither misses table 2
-                const uint32_t two = (u0 & u1) | (u0 & u2) | (u1 & u2);
-                const uint32_t q7 = u0 | u1 | u2;
-                pat[k] = (xa[k] & C6) | (u1 >> 1) | u2;
-                msk7[k] = C6 | (q7 >> 1);
-                msk[k] = msk7[k] | q7;
-                const uint32_t ne = (((xa[k] ^ xb[k]) & C6) + C6) & B6;
-                const uint32_t nz = ((xa[k] & C6) + C6) & B6;
-                val[k] = ((nz & ~ne) << 1) & ~two;
-            }
-#pragma unroll
-            for (uint32_t j = 0; j < GROUP; j++) {
-                if (q >= lim[j]) continue;  // also skips the unit's unused slots (lim = 0)
-                const uint32_t xc[4] = {Cs[j].x, Cs[j].y, Cs[j].z, Cs[j].w};
-                uint32_t hits = 0;
-#pragma unroll
-                for (int k = 0; k < 4; k++) {
-                    // lane of d is zero iff c matches the expected byte under the mask;
-                    // bit 7 of d7 + 0x7F.. flags a nonzero lane of d7 (no carry leaves a lane)
-                    const uint32_t d = (xc[k] ^ pat[k]) & msk[k];
-                    const uint32_t d7 = (xc[k] ^ pat[k]) & msk7[k];
-                    const uint32_t ok = val[k] & ~((d7 + 0x7F7F7F7Fu) | d);
-                    hits = __dp4a(ok, 0x01010101u, hits);  // 128 per counted slot
-                }
-                cnt[j] += hits >> 7;
-            }
-        }
+        group_pass<0>(bm4, lane, tq, kmax, ca, ma, cb, mb, cc, mc, klim, cnt);
+        group_pass<1>(bm4, lane, tq, kmax, ca, ma, cb, mb, cc, mc, klim, cnt);
+        group_pass<2>(bm4, lane, tq, kmax, ca, ma, cb, mb, cc, mc, klim, cnt);
+        group_pass<3>(bm4, lane, tq, kmax, ca, ma, cb, mb, cc, mc, klim, cnt);
 #pragma unroll
         for (uint32_t j = 0; j < GROUP; j++) {
             if (j >= gn) break;
@@ -729,8 +762,9 @@ void frequent_triples(batmap_set *S, uint32_t s, const uint32_t *d_pairs, uint64
     if (nc) {
         const View V{reinterpret_cast<const uint32_t *>(S->d_bm.p), S->d_base.p, S->d_rlog.p, S->d_perm.p,
                      S->d_fail_off.p, S->d_fail_tid.p, S->m, S->n, S->shift};
-        const unsigned grid = (unsigned)std::min<uint64_t>((n_units + 7) / 8, 152ull * 64);
-        k_witness_group<<<grid, 256, 0, st>>>(V, d_pairs, cnt.p, cand.p, units.p, n_units, sup.p);
+        const uint64_t wpb = WG_TPB / 32;
+        const unsigned grid = (unsigned)std::min<uint64_t>((n_units + wpb - 1) / wpb, 152ull * 64);
+        k_witness_group<<<grid, WG_TPB, 0, st>>>(V, d_pairs, cnt.p, cand.p, units.p, n_units, sup.p);
         BM_CHECK_LAUNCH();
     }
     E.record(2, st);
