@@ -459,33 +459,52 @@ __global__ void k_unit_fill(const uint64_t *cand_off, const uint64_t *uoff, uint
 // v: c must miss v; two or more: no c makes T the witness.  This becomes an
 // expected byte pat (a's code; v in the top bits where constrained) under a
 // mask msk (msk7 = msk without bit 7) and a validity flag val (bit 7) for
-// lanes where a and b agree on a nonempty code and the rule can hold.  Bit 7
-// of x holds the high bit of the lane's missing table and bit 7 of x << 1 the
-// low bit.
+// lanes where a and b agree on a nonempty code and the rule can hold.
+//
+// A copy stored in table T never names T as its missing table, so each pass
+// sees only three missing tables M (high bit h at bit 7, low bit l at bit 6):
+//   T = 0: M in {1, 2, 3}; c is always free.
+//   T = 1: M in {0, 2, 3}, M != 0 iff h; if h_a and h_b, c must miss 0,
+//          which for c is h_c = 0.
+//   T = 2: M in {0, 1, 3}, M in {0, 1} iff h = 0; h_a and h_b: both miss 3,
+//          tables 0 and 1 stay open (invalid); h_a = h_b = 0 and l_a != l_b:
+//          a and b miss 0 and 1 (free); otherwise c must miss v = 1 - l of
+//          the set with h = 0 (l_a if h_a = 0, else l_b).
+//   T = 3: M in {0, 1, 2}; valid iff M_a != M_b, and then c must miss the
+//          third one, v = ~(M_a | M_b) (two bits).
 template <int T>
 __device__ __forceinline__ void pair_rule(uint32_t xa, uint32_t xb, uint32_t &pat, uint32_t &msk, uint32_t &msk7,
                                           uint32_t &val) {
-    constexpr uint32_t C6 = 0x3F3F3F3Fu, H7 = 0x80808080u, L7 = 0x7E7E7E7Eu;
+    constexpr uint32_t C6 = 0x3F3F3F3Fu, B6 = 0x40404040u, H7 = 0x80808080u, L7 = 0x7E7E7E7Eu;
+    const uint32_t x = xa ^ xb;
     const uint32_t za = xa & C6;
     // bit 7 of 2 e + 0x7E (e <= 0x3F per lane, no carry leaves a lane) is set iff e != 0
-    const uint32_t ne = ((xa ^ xb) & C6) * 2u + L7;  // codes differ
-    const uint32_t nz = za * 2u + L7;                // slot not empty
+    const uint32_t ne = (x & C6) * 2u + L7;  // codes differ
+    const uint32_t nz = za * 2u + L7;        // slot not empty
     if (T == 0) {
         pat = za;
         msk = msk7 = C6;
         val = nz & ~ne & H7;
-        return;
+    } else if (T == 1) {
+        const uint32_t c7 = xa & xb & H7;  // constrained: c must have h = 0
+        pat = za;
+        msk7 = C6;
+        msk = C6 | c7;
+        val = nz & ~ne & H7;
+    } else if (T == 2) {
+        const uint32_t c7 = (xa | xb | ~(x << 1)) & H7;       // not free
+        const uint32_t sel = xa >> 1;                          // h_a at bit 6
+        const uint32_t l = (sel & xb) | (~sel & xa);           // bit 6: l of the set with h = 0 (a first)
+        pat = za | (~l & B6);
+        msk7 = C6 | (c7 >> 1);
+        msk = msk7 | c7;
+        val = nz & ~(ne | (xa & xb)) & H7;
+    } else {
+        pat = (xa & C6) | (~xa & ~xb & ~C6);  // a's code, v = ~(M_a | M_b)
+        msk = 0xFFFFFFFFu;
+        msk7 = 0x7F7F7F7Fu;
+        val = nz & ~ne & (x | (x << 1)) & H7;  // M_a != M_b
     }
-    const uint32_t a2 = xa << 1, b2 = xb << 1;
-    const uint32_t u0 = (xa | a2) & (xb | b2) & H7;                     // neither misses table 0
-    const uint32_t u1 = T >= 2 ? (xa | ~a2) & (xb | ~b2) & H7 : 0u;     // neither misses table 1
-    const uint32_t u2 = T >= 3 ? (~xa | a2) & (~xb | b2) & H7 : 0u;     // neither misses table 2
-    const uint32_t two = (u0 & u1) | (u0 & u2) | (u1 & u2);
-    const uint32_t q7 = u0 | u1 | u2;
-    pat = za | (u1 >> 1) | u2;
-    msk7 = C6 | (q7 >> 1);
-    msk = msk7 | q7;
-    val = nz & ~ne & ~two & H7;
 }
 
 // One pass of a unit over the chunks of table T.

@@ -15,24 +15,31 @@ import numpy as np
 from oracle import dof_rules as R
 
 M32 = 0xFFFFFFFF
-C6, H7, L7, K7 = 0x3F3F3F3F, 0x80808080, 0x7E7E7E7E, 0x7F7F7F7F
+C6, B6, H7, L7, K7 = 0x3F3F3F3F, 0x40404040, 0x80808080, 0x7E7E7E7E, 0x7F7F7F7F
 
 
 def pair_rule(T, xa, xb):
-    """(pat, msk, msk7, val) of a pair's word for a slot of table T."""
+    """(pat, msk, msk7, val) of a pair's word for a slot of table T.  A copy
+    in table T never names T as its missing table, so each table sees three
+    missing tables and the kernel specialises the reduction per table."""
+    x = xa ^ xb
     za = xa & C6
-    ne = (((xa ^ xb) & C6) * 2 + L7) & M32   # bit 7: codes differ
-    nz = (za * 2 + L7) & M32                 # bit 7: not empty
+    ne = ((x & C6) * 2 + L7) & M32   # bit 7: codes differ
+    nz = (za * 2 + L7) & M32         # bit 7: not empty
     if T == 0:
         return za, C6, C6, nz & ~ne & H7 & M32
-    a2, b2 = (xa << 1) & M32, (xb << 1) & M32
-    u0 = (xa | a2) & (xb | b2) & H7
-    u1 = (xa | (~a2 & M32)) & (xb | (~b2 & M32)) & H7 if T >= 2 else 0
-    u2 = ((~xa & M32) | a2) & ((~xb & M32) | b2) & H7 if T >= 3 else 0
-    two = (u0 & u1) | (u0 & u2) | (u1 & u2)
-    q7 = u0 | u1 | u2
-    msk7 = C6 | (q7 >> 1)
-    return za | (u1 >> 1) | u2, msk7 | q7, msk7, nz & ~ne & ~two & H7 & M32
+    if T == 1:
+        c7 = xa & xb & H7            # both miss 2 or 3: c must miss 0 (high bit 0)
+        return za, C6 | c7, C6, nz & ~ne & H7 & M32
+    if T == 2:
+        c7 = (xa | xb | (~(x << 1) & M32)) & H7       # not free
+        sel = xa >> 1
+        low = (sel & xb) | (~sel & M32 & xa)
+        msk7 = C6 | (c7 >> 1)
+        return (za | (~low & M32 & B6), msk7 | c7, msk7,
+                nz & ~(ne | (xa & xb)) & H7 & M32)
+    pat = (xa & C6) | (~xa & ~xb & ~C6 & M32)
+    return pat, M32, 0x7F7F7F7F, nz & ~ne & (x | ((x << 1) & M32)) & H7 & M32
 
 
 def candidate_ok(T, xa, xb, xc):
