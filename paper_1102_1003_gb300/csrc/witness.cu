@@ -439,6 +439,7 @@ __global__ void k_check_ids(const uint32_t *ids, uint64_t count, uint32_t n, int
 // compile-time case of each pass.
 constexpr uint32_t GROUP = 8;
 constexpr uint32_t WG_TPB = 128;  // threads per block of k_witness_group
+static_assert(GROUP <= 8, "a unit's slot order is kept in four bits per slot of one word");
 
 __global__ void k_unit_counts(const uint64_t *cand_off, uint64_t np, uint64_t *ucnt) {
     for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < np;
@@ -530,7 +531,7 @@ __device__ __forceinline__ void group_pass(const uint4 *__restrict__ bm4, uint32
         for (int w = 0; w < 4; w++) pair_rule<T>(xa[w], xb[w], pat[w], msk[w], msk7[w], val[w]);
 #pragma unroll
         for (uint32_t j = 0; j < GROUP; j++) {
-            if (k >= klim[j]) continue;  // also skips the unit's unused slots (klim = 0)
+            if (k >= klim[j]) break;  // sorted: the rest of the unit has ended too (unused slots: klim = 0)
             const uint32_t xc[4] = {Cs[j].x, Cs[j].y, Cs[j].z, Cs[j].w};
             uint32_t hits = 0;
 #pragma unroll
@@ -590,18 +591,43 @@ __global__ void __launch_bounds__(WG_TPB) k_witness_group(View V, const uint32_t
             }
             kmax = max(kmax, klim[j]);
         }
+        // Order the unit by decreasing klim (odd-even transposition sort), so
+        // the candidates still running at chunk k are a prefix; pos holds the
+        // original slot of each (four bits per slot).
+        uint32_t pos = 0;
+#pragma unroll
+        for (uint32_t j = 0; j < GROUP; j++) pos |= j << (4 * j);
+#pragma unroll
+        for (uint32_t r = 0; r < GROUP; r++) {
+#pragma unroll
+            for (uint32_t j = r & 1u; j + 1 < GROUP; j += 2) {
+                if (klim[j] < klim[j + 1]) {
+                    const uint32_t tk = klim[j], tm = mc[j];
+                    const uint64_t tc = cc[j];
+                    klim[j] = klim[j + 1];
+                    mc[j] = mc[j + 1];
+                    cc[j] = cc[j + 1];
+                    klim[j + 1] = tk;
+                    mc[j + 1] = tm;
+                    cc[j + 1] = tc;
+                    const uint32_t f = ((pos >> (4 * j)) ^ (pos >> (4 * j + 4))) & 15u;
+                    pos ^= (f << (4 * j)) | (f << (4 * j + 4));
+                }
+            }
+        }
         group_pass<0>(bm4, lane, tq, kmax, ca, ma, cb, mb, cc, mc, klim, cnt);
         group_pass<1>(bm4, lane, tq, kmax, ca, ma, cb, mb, cc, mc, klim, cnt);
         group_pass<2>(bm4, lane, tq, kmax, ca, ma, cb, mb, cc, mc, klim, cnt);
         group_pass<3>(bm4, lane, tq, kmax, ca, ma, cb, mb, cc, mc, klim, cnt);
 #pragma unroll
         for (uint32_t j = 0; j < GROUP; j++) {
-            if (j >= gn) break;
-            const uint32_t it[3] = {a, b, cand[3 * (c0 + j) + 2]};
+            if (j >= gn) break;  // unused slots (klim = 0) sort last
+            const uint32_t o = (pos >> (4 * j)) & 15u;
+            const uint32_t it[3] = {a, b, cand[3 * (c0 + o) + 2]};
             uint32_t v = cnt[j] + failed_common<3>(V, it, lane);
 #pragma unroll
             for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
-            if (lane == 0) sup[c0 + j] = v;
+            if (lane == 0) sup[c0 + o] = v;
         }
     }
 }
