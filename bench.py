@@ -156,6 +156,31 @@ def cpu_oracle_rate(inst, seconds: float, seed: int = 0):
     return k / dt, cores, k, dt
 
 
+def merge_micro(n: int = 1 << 24, repeats: int = 5):
+    """Sec. IV-B's merging experiment on this host: count the identical elements
+    of two sorted arrays of n 32-bit integers with the oracle's single-threaded
+    merge, on one core and as simultaneous runs on every core.  Returns set
+    elements (2 n per merge) per second for both."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    a, b = datagen.sorted_u32(n, 1), datagen.sorted_u32(n, 2)
+    common = oracle.intersect_count(a, b)
+    assert common == np.intersect1d(a, b, assume_unique=True).size
+    t0 = time.perf_counter()
+    for _ in range(repeats):
+        oracle.intersect_count(a, b)
+    one = 2 * n * repeats / (time.perf_counter() - t0)
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(cores) as ex:  # ctypes releases the GIL during each merge
+        list(ex.map(lambda _: [oracle.intersect_count(a, b) for _ in range(repeats)], range(cores)))
+    par = 2 * n * repeats * cores / (time.perf_counter() - t0)
+    return {"n": n, "repeats": repeats, "elements_per_s_1core": one, "elements_per_s_all_cores": par,
+            "cores": cores, "common": int(common),
+            "inputs": "two sorted uint32 arrays, gaps uniform in [1, 255], seeds 1 and 2",
+            "paper_context": "Sec. IV-B on its own CPU: 2.25e8 elements/s on one core, 1.71e9 on 8"}
+
+
 def run_reference(args, inst, rank, world):
     if rank != 0:
         return
@@ -331,6 +356,8 @@ def run_mine(args, inst, rank, world):
         "logical_hbm": {"achieved_GBps": logical_gbs, "peak_GBps": peaks["hbm_gbs"],
                         "frac": logical_gbs / peaks["hbm_gbs"],
                         "definition": "sum over pairs of 2*max(|B_i|,|B_j|) bytes / compare time (Sec. IV-A)"},
+        "set_elements_per_s": (inst.n - 1) * int(inst.tids.size) / cmp_s,
+        "set_elements_definition": "sum over pairs of |S_i| + |S_j| = (n-1) * tids, per compare time (Sec. IV-B)",
         "phases_ms": {"build": statistics.mean(build_ms), "compare": statistics.mean(compare_ms),
                       "correct_compact": statistics.mean(compact_ms)},
         "frequent_pairs": n_out, "failed_insertions": info["n_failed"],
@@ -346,7 +373,8 @@ def run_mine(args, inst, rank, world):
         rate, cores, k, dt = cpu_oracle_rate(inst, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": f"{k} uniformly sampled pairs of the same workload, {dt:.1f} s "
-                                          "(single-threaded sorted merge on disjoint blocks, one per core)"}
+                                          "(single-threaded sorted merge on disjoint blocks, one per core)",
+                                "merge_micro": merge_micro()}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -154,6 +154,15 @@ WORKLOADS = {
 }
 
 
+def sorted_u32(count: int, seed: int, max_gap: int = 255) -> np.ndarray:
+    """Strictly increasing uint32 values with independent gaps uniform in
+    [1, max_gap] (two such arrays interleave at random)."""
+    g = np.random.default_rng([seed, 0x5E7])
+    vals = np.cumsum(g.integers(1, max_gap + 1, size=count, dtype=np.uint64))
+    assert vals[-1] < 2 ** 32
+    return vals.astype(np.uint32)
+
+
 def workload_instance(name: str, scale_n: int | None = None) -> Instance:
     """Instance of a named workload; `scale_n` truncates the item count."""
     c = WORKLOADS[name]

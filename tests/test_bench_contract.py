@@ -23,3 +23,17 @@ def test_reference_arm_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["config"]["workload"] == "zipf_m1m_n2000"
+
+
+def test_merge_micro_small():
+    # the Sec. IV-B merging experiment at a small size: the count is exact and
+    # the rates are positive
+    sys.path.insert(0, ROOT)
+    import bench
+    import datagen
+    import numpy as np
+    r = bench.merge_micro(n=1 << 16, repeats=1)
+    a, b = datagen.sorted_u32(1 << 16, 1), datagen.sorted_u32(1 << 16, 2)
+    assert r["common"] == len(set(a.tolist()) & set(b.tolist()))
+    assert np.all(np.diff(a.astype(np.int64)) > 0)
+    assert r["elements_per_s_1core"] > 0 and r["elements_per_s_all_cores"] > 0 and r["cores"] >= 1
