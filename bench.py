@@ -104,18 +104,26 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def _traffic_record():
-    """DRAM bytes per compare launch from the committed ncu summary, or None if
-    the kernel source changed since it was taken."""
-    path = os.path.join(ROOT, "profiles", "compare_traffic.json")
+def _traffic_record(workload: str, record: str = "compare_traffic.json", source: str = "compare.cu"):
+    """DRAM bytes per launch of a kernel from a committed ncu record, or None if
+    the record is for another workload or the kernel's source file changed
+    since it was taken."""
+    path = os.path.join(ROOT, "profiles", record)
     try:
         rec = json.load(open(path))
     except (OSError, ValueError):
         return None
-    src = open(os.path.join(ROOT, "paper_1102_1003_gb300", "csrc", "compare.cu"), "rb").read()
-    if rec.get("compare_cu_sha256") != hashlib.sha256(src).hexdigest():
+    src = open(os.path.join(ROOT, "paper_1102_1003_gb300", "csrc", source), "rb").read()
+    if rec.get(source.replace(".", "_") + "_sha256") != hashlib.sha256(src).hexdigest():
+        return None
+    if rec.get("workload") != workload:
         return None
     return rec
+
+
+def _traffic(workload: str, record: str = "compare_traffic.json", source: str = "compare.cu"):
+    rec = _traffic_record(workload, record, source)
+    return rec["traffic_bytes_per_launch"] if rec else None
 
 
 def max_over_ranks(value: float, device=None) -> float:
@@ -243,6 +251,7 @@ def dense_leg(args, inst, off, tids, n_out_ref, peaks, peak_kind):
             "phases_ms": {"bitmap": statistics.mean(build), "tensor_kernel": statistics.mean(gemm)},
             "roofline": {"bound": "tensor", "achieved": flops_issued / g / 1e12, "peak": peak, "unit": "TFLOP/s",
                          "frac": flops_issued / g / 1e12 / peak, "kernel": "k_dense_mmt",
+                         "traffic": _traffic(args.workload, "dense_traffic.json", "dense.cu"),
                          "peak_kind": f"e4m3 dense = 2 x {peak_kind} bf16 burst (nominal 4.5/2.25 ratio)",
                          "algorithmic_TFLOPs": flops_alg / g / 1e12},
             "dtype": "e4m3 {0,1} operands, fp32 accumulate (exact integers < 2^24)"}
@@ -338,7 +347,6 @@ def run_mine(args, inst, rank, world):
     alu_peak = sms * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12  # Tops/s
     achieved = OPS_PER_WORD_PAIR * wp / cmp_s / 1e12
     logical_gbs = 8.0 * wp / cmp_s / 1e9
-    trec = _traffic_record()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
@@ -349,7 +357,7 @@ def run_mine(args, inst, rank, world):
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
                      "frac": achieved / alu_peak, "kernel": "k_compare",
-                     "traffic": (trec["traffic_bytes_per_launch"] if trec else None),
+                     "traffic": _traffic(args.workload),
                      "peak_kind": f"{sms} SMs x 128 INT32 lanes x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz "
                                   f"({peak_kind} max clock)",
                      "algorithmic_ops": f"{OPS_PER_WORD_PAIR} x {wp:.4g} word pairs"},
@@ -698,7 +706,8 @@ def run_triples(args):
                           "witness": 1e3 * wit_s,
                           "candidates_compact": statistics.mean(r[4]["compact_ms"] for r in rec)},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
-                         "frac": achieved / alu_peak, "kernel": "k_witness_group", "traffic": None,
+                         "frac": achieved / alu_peak, "kernel": "k_witness_group",
+                         "traffic": _traffic("triples", "witness_traffic.json", "witness.cu"),
                          "peak_kind": f"{sms} SMs x 128 INT32 lanes x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz "
                                       f"({peak_kind} max clock)",
                          "algorithmic_ops": f"{WITNESS_OPS} x {wt:.4g} word-triples (max_j r_j words per candidate)",
