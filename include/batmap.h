@@ -22,6 +22,12 @@
  *     of the last error on the calling thread is batmap_last_error().  No C++
  *     exception crosses this interface.  On error, outputs are unspecified
  *     except where a call documents otherwise.
+ *   - One GPU per process.  The library's one-time setup (kernel shared-memory
+ *     limits, the SM count, cached placement scratch and BatMap arrays) is
+ *     made on the device current at the first call; every later call must
+ *     run with that device current.  Drive several GPUs with one process per
+ *     GPU (bench.py under torchrun does).  A handle (set or pool) is used by
+ *     one host thread at a time; batmap_serve runs its own request loop.
  */
 #ifndef BATMAP_H
 #define BATMAP_H

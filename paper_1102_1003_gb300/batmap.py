@@ -172,6 +172,28 @@ def _stream_handle(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
+_device = None  # the one GPU this process's library works on (set at first use)
+
+
+def _current_device() -> int:
+    import torch
+    return torch.cuda.current_device()
+
+
+def _check_device(index: int) -> None:
+    """The library works on the current device and on one GPU per process: a
+    tensor on another device, or a second GPU, is refused here."""
+    global _device
+    cur = _current_device()
+    if index != cur:
+        raise ValueError(f"tensor on cuda:{index} but cuda:{cur} is current; the library works on the "
+                         "current device")
+    if _device is None:
+        _device = index
+    elif index != _device:
+        raise ValueError(f"this process already uses cuda:{_device}; the library serves one GPU per process")
+
+
 def _ptr(t):
     """Device pointer of a contiguous CUDA tensor of 4- or 8-byte elements (None -> NULL).
     The library reads raw memory, so a strided view or a host tensor is refused here."""
@@ -183,6 +205,7 @@ def _ptr(t):
         raise ValueError("expected a contiguous tensor")
     if t.element_size() not in (4, 8):
         raise ValueError(f"expected 4- or 8-byte elements, got {t.dtype}")
+    _check_device(t.device.index)
     return ctypes.c_void_p(t.data_ptr())
 
 

@@ -91,3 +91,35 @@ def test_binding_refuses_malformed_tensors(lib):
         batmap.batmap_build_d(3, 10, off, tids, perm)                     # d = 3 needs four rows
     with pytest.raises(ValueError):
         batmap.batmap_build(10, off, tids, perm)                          # host tensors
+
+
+def test_binding_refuses_a_second_device(monkeypatch):
+    # the library serves one GPU per process and works on the current device;
+    # a stand-in tensor object exercises the check without a GPU
+    from paper_1102_1003_gb300 import batmap
+
+    class FakeCuda:
+        is_cuda = True
+        dtype = "int32"
+
+        def __init__(self, index):
+            self.device = type("D", (), {"index": index})()
+
+        def is_contiguous(self):
+            return True
+
+        def element_size(self):
+            return 4
+
+        def data_ptr(self):
+            return 4096
+
+    current = {"dev": 0}
+    monkeypatch.setattr(batmap, "_current_device", lambda: current["dev"])
+    monkeypatch.setattr(batmap, "_device", None)
+    assert batmap._ptr(FakeCuda(0)).value == 4096
+    with pytest.raises(ValueError, match="is current"):
+        batmap._ptr(FakeCuda(1))          # not the current device
+    current["dev"] = 1
+    with pytest.raises(ValueError, match="one GPU per process"):
+        batmap._ptr(FakeCuda(1))          # a second GPU in the same process
