@@ -8,9 +8,12 @@ correction and the support-threshold compaction, ending with the number of
 frequent pairs on the host.  The metric is pair supports per second
 (n(n-1)/2 per step).
 
-Default workload: m = 1,000,000 transactions, n = 2,000 items, Zipf(1) item
-frequencies at mean density 2%, s = 1,000 (0.1% of m); inputs (160 MB of
-tids) and BatMaps (331 MB) exceed the 129 MB L2, so no flush is needed.
+Default workload: the density sweep at scale, m = 4,194,304 transactions,
+n = 8,192 items, Bernoulli density 5% (1.7e9 tids, 12.9 GB of BatMaps, all
+33,550,336 pair supports); inputs exceed the 129 MB L2, so no flush is
+needed.  The same line carries, as sub-records, the Zipf workload (m = 10^6,
+n = 2,000) and the batched form against plain per-instance calls on 64
+instances of uneven size.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
     python bench.py --impl reference ...   # the CPU oracle on the same metric
@@ -217,20 +220,22 @@ def run_reference(args, inst, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def dense_leg(args, inst, off, tids, n_out_ref, peaks, peak_kind):
+def dense_leg(args, inst, off, tids, n_out_ref, peaks, peak_kind, steps=None, warmup=None, workload=None):
     """The dense-bitmap tensor-core comparison path on the same workload."""
     import torch
     import paper_1102_1003_gb300 as pkg
+    steps = args.steps if steps is None else steps
+    warmup = args.warmup if warmup is None else warmup
     npairs = inst.n * (inst.n - 1) // 2
     pairs = torch.empty((max(n_out_ref, 1), 3), dtype=torch.int32, device=off.device)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         pkg.pair_support_dense(inst.m, off, tids, inst.s, pairs=pairs)
     stream = torch.cuda.current_stream()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     gemm, build = [], []
     ev0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         k, _, t = pkg.pair_support_dense(inst.m, off, tids, inst.s, pairs=pairs)
         gemm.append(t["compare_ms"])
         build.append(t["build_ms"])
@@ -243,52 +248,47 @@ def dense_leg(args, inst, off, tids, n_out_ref, peaks, peak_kind):
     tiles = 2 * sum(min((n + 2 * bm - 1) // (2 * bm), bj + 1) for bj in range((n + bn - 1) // bn))
     kpad = (inst.m + 127) // 128 * 128
     flops_issued = 2.0 * tiles * bm * bn * kpad
-    flops_alg = 2.0 * npairs * inst.m
+    flops_alg = 2.0 * npairs * inst.m  # 2 m per pair i < j
     g = statistics.mean(gemm) / 1e3
     # e4m3 dense peak: the measured bf16 peak x the nominal fp8 / bf16 ratio (4.5 / 2.25)
     peak = 2.0 * peaks.get("bf16_tflops", 1900.0)
-    return {"value": npairs * args.steps / elapsed, "unit": UNIT, "ms_per_step": 1e3 * elapsed / args.steps,
+    return {"value": npairs * steps / elapsed, "unit": UNIT, "ms_per_step": 1e3 * elapsed / steps,
             "phases_ms": {"bitmap": statistics.mean(build), "tensor_kernel": statistics.mean(gemm)},
-            "roofline": {"bound": "tensor", "achieved": flops_issued / g / 1e12, "peak": peak, "unit": "TFLOP/s",
-                         "frac": flops_issued / g / 1e12 / peak, "kernel": "k_dense_mmt",
-                         "traffic": _traffic(args.workload, "dense_traffic.json", "dense.cu"),
+            "roofline": {"bound": "tensor", "achieved": flops_alg / g / 1e12, "peak": peak, "unit": "TFLOP/s",
+                         "frac": flops_alg / g / 1e12 / peak, "kernel": "k_dense_mmt",
+                         "traffic": _traffic(workload or args.workload, "dense_traffic.json", "dense.cu"),
                          "peak_kind": f"e4m3 dense = 2 x {peak_kind} bf16 burst (nominal 4.5/2.25 ratio)",
-                         "algorithmic_TFLOPs": flops_alg / g / 1e12},
+                         "algorithmic_flops": "2 m n(n-1)/2 (pairs i < j only)",
+                         "issued_TFLOPs": flops_issued / g / 1e12,
+                         "issued_frac": flops_issued / g / 1e12 / peak},
             "dtype": "e4m3 {0,1} operands, fp32 accumulate (exact integers < 2^24)"}
 
 
-def run_mine(args, inst, rank, world):
+def _alu_peak(dev, peaks):
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    return sms * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12, sms
+
+
+def plain_leg(inst, dev, steps, warmup, peaks, peak_kind, workload, sampler=None, dist=None):
+    """Time `steps` plain steps (batmap_build + pair_support_all) on resident tidlists."""
     import torch
     import paper_1102_1003_gb300 as pkg
     from paper_1102_1003_gb300 import batmap as B
-
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
     L = pkg.load_library()
-    perm_np = datagen.permutations(inst.m, seed=2)
     off = torch.from_numpy(inst.offsets.astype(np.int64)).to(dev)
-    tids = torch.from_numpy(inst.tids.astype(np.int32)).to(dev)
-    perm = torch.from_numpy(perm_np.astype(np.int32)).to(dev)
-    stream = torch.cuda.current_stream()
+    tids = torch.from_numpy(inst.tids.view(np.int32)).to(dev)
     npairs = inst.n * (inst.n - 1) // 2
-
-    # size the output once
-    bset = pkg.batmap_build(inst.m, off, tids, perm)
+    bset = pkg.batmap_build(inst.m, off, tids, None)
     n_out, _ = pkg.pair_support_all(bset, inst.s)
     info = bset.info
     bset.free()
     pairs_buf = torch.empty((max(n_out, 1), 3), dtype=torch.int32, device=dev)
-
     timing = B.batmap_timing()
     compare_ms, build_ms, compact_ms = [], [], []
 
     def step(record):
-        bs = pkg.batmap_build(inst.m, off, tids, perm)
+        bs = pkg.batmap_build(inst.m, off, tids, None)
         k, _ = pkg.pair_support_all(bs, inst.s, pairs=pairs_buf)
         if record:
             L.batmap_get_timing(bs.handle, ctypes.byref(timing))
@@ -298,17 +298,18 @@ def run_mine(args, inst, rank, world):
         bs.free()
         return k
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step(False)
-    sampler = ClockSampler(local)
-    sampler.start()
+    if sampler:
+        sampler.start()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     launches0 = L.batmap_kernel_launches()
+    stream = torch.cuda.current_stream()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         got = step(True)
     ev1.record(stream)
     torch.cuda.synchronize()
@@ -317,47 +318,22 @@ def run_mine(args, inst, rank, world):
     if dist:
         elapsed = max_over_ranks(elapsed, dev)
         dist.barrier()
-    clocks = sampler.stop()
+    clocks = sampler.stop() if sampler else None
     assert got == n_out
-
-    # end to end through the C ABI from pinned host buffers
-    h_off = torch.from_numpy(inst.offsets.astype(np.uint64).view(np.int64)).pin_memory().numpy().view(np.uint64)
-    h_tids = torch.from_numpy(inst.tids.view(np.int32)).pin_memory().numpy().view(np.uint32)
-    h_perm = torch.from_numpy(perm_np.view(np.int32)).pin_memory().numpy().view(np.uint32)
-    h_pairs = torch.empty(3 * max(n_out, 1), dtype=torch.int32).pin_memory().numpy()
-    e2e_steps = max(2, min(args.steps, 5))
-    pkg.pair_support_host(inst.m, h_off, h_tids, h_perm, inst.s, h_pairs)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        k = pkg.pair_support_host(inst.m, h_off, h_tids, h_perm, inst.s, h_pairs)
-    e2e_t = (time.perf_counter() - t0) / e2e_steps
-    assert k == n_out
-
-    if rank != 0:
-        if dist:
-            dist.destroy_process_group()
-        return
-
-    peaks, peak_kind = _peaks()
-    value = world * npairs * args.steps / elapsed
     cmp_s = statistics.mean(compare_ms) / 1e3
     wp = info["word_pairs"]
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    alu_peak = sms * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12  # Tops/s
+    alu_peak, sms = _alu_peak(dev, peaks)
     achieved = OPS_PER_WORD_PAIR * wp / cmp_s / 1e12
     logical_gbs = 8.0 * wp / cmp_s / 1e9
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": args.workload, "desc": WORKLOAD_DESC[args.workload], "m": inst.m, "n": inst.n,
+    rec = {
+        "value": npairs * steps / elapsed, "unit": UNIT, "steps": steps, "warmup": warmup,
+        "ms_per_step": 1e3 * elapsed / steps, "elapsed_s": elapsed,
+        "config": {"workload": workload, "desc": WORKLOAD_DESC[workload], "m": inst.m, "n": inst.n,
                    "s": inst.s, "pairs": npairs, "tids": int(inst.tids.size), "batmap_bytes": info["bytes"],
-                   "width_classes": info["n_classes"], "l2": "inputs larger than L2 (no flush)",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+                   "width_classes": info["n_classes"], "l2": "inputs larger than L2 (no flush)"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
                      "frac": achieved / alu_peak, "kernel": "k_compare",
-                     "traffic": _traffic(args.workload),
+                     "traffic": _traffic(workload),
                      "peak_kind": f"{sms} SMs x 128 INT32 lanes x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz "
                                   f"({peak_kind} max clock)",
                      "algorithmic_ops": f"{OPS_PER_WORD_PAIR} x {wp:.4g} word pairs"},
@@ -365,89 +341,169 @@ def run_mine(args, inst, rank, world):
                         "frac": logical_gbs / peaks["hbm_gbs"],
                         "definition": "sum over pairs of 2*max(|B_i|,|B_j|) bytes / compare time (Sec. IV-A)"},
         "set_elements_per_s": (inst.n - 1) * int(inst.tids.size) / cmp_s,
-        "set_elements_definition": "sum over pairs of |S_i| + |S_j| = (n-1) * tids, per compare time (Sec. IV-B)",
         "phases_ms": {"build": statistics.mean(build_ms), "compare": statistics.mean(compare_ms),
                       "correct_compact": statistics.mean(compact_ms)},
-        "frequent_pairs": n_out, "failed_insertions": info["n_failed"],
-        "gpu_launches": int(launches),
-        "e2e": {"value": npairs / e2e_t, "unit": UNIT,
-                "h2d_bytes_per_step": int(h_off.nbytes + h_tids.nbytes + h_perm.nbytes),
-                "d2h_bytes_per_step": int(12 * n_out + 8)},
+        "frequent_pairs": n_out, "failed_insertions": info["n_failed"], "gpu_launches": int(launches),
         "clocks": clocks,
+    }
+    return rec, off, tids, n_out
+
+
+def run_mine(args, inst, rank, world):
+    import torch
+    import paper_1102_1003_gb300 as pkg
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    pkg.load_library()
+    peaks, peak_kind = _peaks()
+    npairs = inst.n * (inst.n - 1) // 2
+    rec, off, tids, n_out = plain_leg(inst, dev, args.steps, args.warmup, peaks, peak_kind, args.workload,
+                                      sampler=ClockSampler(local), dist=dist)
+
+    # end to end through the C ABI from pinned host buffers (library-made permutations)
+    h_off = torch.from_numpy(inst.offsets.astype(np.uint64).view(np.int64)).pin_memory().numpy().view(np.uint64)
+    h_tids = torch.from_numpy(inst.tids.view(np.int32)).pin_memory().numpy().view(np.uint32)
+    h_pairs = torch.empty(3 * max(n_out, 1), dtype=torch.int32).pin_memory().numpy()
+    e2e_steps = max(2, min(args.steps, 5))
+    pkg.pair_support_host(inst.m, h_off, h_tids, None, inst.s, h_pairs)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        k = pkg.pair_support_host(inst.m, h_off, h_tids, None, inst.s, h_pairs)
+    e2e_t = (time.perf_counter() - t0) / e2e_steps
+    assert k == n_out
+    del h_tids
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    line = {
+        "metric": METRIC, "value": world * rec["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": rec["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": dict(rec["config"], parallelism="replicas" if world > 1 else "single GPU"),
+        "roofline": rec["roofline"], "logical_hbm": rec["logical_hbm"],
+        "set_elements_per_s": rec["set_elements_per_s"],
+        "set_elements_definition": "sum over pairs of |S_i| + |S_j| = (n-1) * tids, per compare time (Sec. IV-B)",
+        "phases_ms": rec["phases_ms"], "frequent_pairs": n_out, "failed_insertions": rec["failed_insertions"],
+        "gpu_launches": rec["gpu_launches"],
+        "e2e": {"value": npairs / e2e_t, "unit": UNIT,
+                "h2d_bytes_per_step": int(h_off.nbytes + 4 * inst.tids.size),
+                "d2h_bytes_per_step": int(12 * n_out + 8)},
+        "clocks": rec["clocks"],
     }
     if not args.no_dense and inst.m <= (1 << 24):
         line["dense"] = dense_leg(args, inst, off, tids, n_out, peaks, peak_kind)
+    del off, tids
+    pkg.batmap_release_scratch()
+    torch.cuda.empty_cache()
     if world == 1 and not args.no_cpu_baseline:
         rate, cores, k, dt = cpu_oracle_rate(inst, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": f"{k} uniformly sampled pairs of the same workload, {dt:.1f} s "
                                           "(single-threaded sorted merge on disjoint blocks, one per core)",
                                 "merge_micro": merge_micro()}
+    if world == 1 and not args.no_sub:
+        sub = {}
+        if args.workload != "zipf_m1m_n2000":
+            z = datagen.workload_instance("zipf_m1m_n2000")
+            zr, zoff, ztids, zn = plain_leg(z, dev, 5, 3, peaks, peak_kind, "zipf_m1m_n2000")
+            zr["dense"] = dense_leg(args, z, zoff, ztids, zn, peaks, peak_kind, steps=5, warmup=3,
+                                    workload="zipf_m1m_n2000")
+            del zoff, ztids
+            sub["zipf_m1m_n2000"] = zr
+        pkg.batmap_release_scratch()
+        torch.cuda.empty_cache()
+        sub["batched"] = batch_record(args, steps=3, warmup=2)
+        line["sub"] = sub
+        line["extra_keys"] = sorted(k for k in line if k not in (
+            "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+            "scaling", "vs_baseline", "dtype", "data", "config", "roofline", "cpu_baseline", "e2e",
+            "gpu_launches", "clocks"))
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
 
 
-def run_batch(args):
-    """Batched workload: 64 instances (m log-uniform in [1e4, 1e6], n uniform in
-    [100, 4000], density uniform in [1%, 10%], Zipf items); one batched,
-    graph-captured persistent launch vs 64 plain pair_support_all calls."""
+def batch_record(args, steps, warmup, small=False, instances=64, autotune=True):
+    """Batched form: `instances` independent instances (m log-uniform in [1e4, 1e6],
+    n uniform in [100, 4000], density uniform in [1%, 10%], Zipf items); one batched,
+    graph-captured persistent pass vs the same instances as plain pair_support_all
+    calls, each timed with events; outputs compared, a sample against the oracle."""
     import torch
     import paper_1102_1003_gb300 as pkg
     import oracle
-    torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
-    if args.batch_small:
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if small:
         # many small instances, where per-call launches and synchronisations dominate
-        specs = datagen.batch_specs(args.instances, 5000, m_range=(1e3, 1e5), n_range=(50, 400))
+        specs = datagen.batch_specs(instances, 5000, m_range=(1e3, 1e5), n_range=(50, 400))
     else:
-        specs = datagen.batch_specs(args.instances, 1000)
+        specs = datagen.batch_specs(instances, 1000)
     t0 = time.perf_counter()
     insts = datagen.batch_instances(specs, workers=os.cpu_count() or 8)
     gen_s = time.perf_counter() - t0
-    sets, bufs, npairs = [], [], 0
+    sets, npairs, wp = [], 0, 0.0
     t0 = time.perf_counter()
-    for q, inst in enumerate(insts):
+    for inst in insts:
         off = torch.from_numpy(inst.offsets.view(np.int64)).to(dev)
         tids = torch.from_numpy(inst.tids.view(np.int32)).to(dev)
-        perm = torch.from_numpy(datagen.permutations(inst.m, inst.s + q).view(np.int32)).to(dev)
-        sets.append(pkg.batmap_build(inst.m, off, tids, perm))
+        sets.append(pkg.batmap_build(inst.m, off, tids, None))
         npairs += inst.n * (inst.n - 1) // 2
-        del off, tids, perm
+        del off, tids
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
+    eff = pkg.batmap_autotune(sets) if autotune else None
+    wp = sum(b.info["word_pairs"] for b in sets)
     # output sizes from one plain pass
     n_out = [pkg.pair_support_all(b, i.s)[0] for b, i in zip(sets, insts)]
     bufs = [torch.empty((max(k, 1), 3), dtype=torch.int32, device=dev) for k in n_out]
     s_list = [i.s for i in insts]
-    eff = None
-    if not args.no_autotune:
-        eff = pkg.batmap_autotune(sets)
+    cmp_plain, cmp_batch = [], []
 
-    def plain():
-        return [pkg.pair_support_all(b, s, pairs=buf)[0] for b, s, buf in zip(sets, s_list, bufs)]
+    def plain(record):
+        got = [pkg.pair_support_all(b, s, pairs=buf)[0] for b, s, buf in zip(sets, s_list, bufs)]
+        if record:
+            cmp_plain.append(sum(pkg.batmap_get_timing(b)["compare_ms"] for b in sets))
+        return got
 
-    def batched():
-        return pkg.pair_support_batch(sets, s_list, bufs)
+    def batched(record):
+        got = pkg.pair_support_batch(sets, s_list, bufs)
+        if record:
+            cmp_batch.append(pkg.batmap_get_timing(sets[0])["compare_ms"])
+        return got
 
     results = {}
     for name, fn in (("plain", plain), ("batched", batched)):
-        for _ in range(args.warmup):
-            fn()
+        for _ in range(warmup):
+            fn(False)
         torch.cuda.synchronize()
         stream = torch.cuda.current_stream()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        for _ in range(args.steps):
-            got = fn()
+        for _ in range(steps):
+            got = fn(True)
         ev1.record(stream)
         torch.cuda.synchronize()
         el = ev0.elapsed_time(ev1) / 1e3
-        results[name] = {"value": npairs * args.steps / el, "ms_per_step": 1e3 * el / args.steps}
+        results[name] = {"value": npairs * steps / el, "ms_per_step": 1e3 * el / steps}
         assert list(got) == n_out, name
+    peaks, peak_kind = _peaks()
+    alu_peak, sms = _alu_peak(dev, peaks)
+    for name, c in (("plain", cmp_plain), ("batched", cmp_batch)):
+        t = statistics.mean(c) / 1e3
+        results[name]["compare_ms"] = 1e3 * t
+        results[name]["compare_lane_op_frac"] = OPS_PER_WORD_PAIR * wp / t / 1e12 / alu_peak
     # batched and plain give identical outputs; a sampled oracle check per instance
     batch_pairs = [b[:k].cpu().numpy().copy() for b, k in zip(bufs, n_out)]
-    plain()
+    plain(False)
     same = all(np.array_equal(b[:k].cpu().numpy(), bp) for b, k, bp in zip(bufs, n_out, batch_pairs))
     rng = np.random.default_rng(3)
     exact = True
@@ -460,17 +516,30 @@ def run_batch(args):
         ref = oracle.pairs_list(inst.offsets, inst.tids, ii, jj, threads=os.cpu_count() or 4)
         idx = ii * inst.n - ii * (ii + 1) // 2 + (jj - ii - 1)
         exact &= bool(np.array_equal(full.cpu().numpy()[idx].astype(np.uint32), ref))
-    line = {"metric": METRIC, "workload": "batch", "unit": UNIT, "value": results["batched"]["value"],
-            "ms_per_step": results["batched"]["ms_per_step"], "plain": results["plain"],
+    for b in sets:
+        b.free()
+    pkg.batmap_release_scratch()
+    torch.cuda.empty_cache()
+    return {"workload": "batch", "unit": UNIT, "value": results["batched"]["value"],
+            "ms_per_step": results["batched"]["ms_per_step"], "steps": steps, "warmup": warmup,
+            "batched": results["batched"], "plain": results["plain"],
             "speedup_batched_over_plain": results["batched"]["value"] / results["plain"]["value"],
-            "config": {"instances": len(insts), "small": bool(args.batch_small), "pairs": npairs,
-                       "tids": int(sum(i.tids.size for i in insts)),
+            "config": {"instances": len(insts), "small": bool(small), "pairs": npairs,
+                       "tids": int(sum(i.tids.size for i in insts)), "word_pairs": wp,
                        "m_range": [min(i.m for i in insts), max(i.m for i in insts)],
                        "n_range": [min(i.n for i in insts), max(i.n for i in insts)],
                        "autotuned": eff is not None},
             "shape_eff": eff, "gen_s": gen_s, "build_s": build_s,
             "batched_equals_plain": same, "oracle_sample_exact": exact}
-    print(json.dumps(line), flush=True)
+
+
+def run_batch(args):
+    """Batched workload: one JSON line (see batch_record)."""
+    import torch
+    torch.cuda.set_device(0)
+    rec = batch_record(args, args.steps, args.warmup, small=args.batch_small, instances=args.instances,
+                       autotune=not args.no_autotune)
+    print(json.dumps(dict({"metric": METRIC}, **rec)), flush=True)
 
 
 def run_nsweep(args):
@@ -810,7 +879,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["mine", "reference"], default="mine")
-    ap.add_argument("--workload", choices=sorted(WORKLOAD_DESC) + ["serve", "batch", "nsweep", "cross", "triples"], default="zipf_m1m_n2000")
+    ap.add_argument("--workload", choices=sorted(WORKLOAD_DESC) + ["serve", "batch", "nsweep", "cross", "triples"], default="bern_m4m_n8192_p5")
     ap.add_argument("--nsweep", type=int, nargs="+", default=[1000, 2000, 4000, 8000, 16000, 32000, 64000])
     ap.add_argument("--instances", type=int, default=64, help="instances (batch workload)")
     ap.add_argument("--batch-small", action="store_true",
@@ -823,6 +892,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-dense", action="store_true", help="skip the dense tensor-core comparison leg")
+    ap.add_argument("--no-sub", action="store_true",
+                    help="skip the sub-records (Zipf workload, batched vs plain) of the default line")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -831,7 +902,7 @@ def main():
             {"serve": run_serve, "batch": run_batch, "nsweep": run_nsweep, "cross": run_cross,
              "triples": run_triples}[args.workload](args)
         return
-    inst = datagen.workload_instance(args.workload)
+    inst = datagen.workload_instance(args.workload, workers=os.cpu_count() or 8)
     if args.impl == "reference":
         run_reference(args, inst, rank, world)
     else:

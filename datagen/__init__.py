@@ -93,9 +93,53 @@ def from_lists(lists, m: int, s: int = 0, name: str = "") -> Instance:
     return Instance(m=m, n=n, offsets=offsets, tids=tids.astype(np.uint32), s=s, name=name)
 
 
-def bernoulli_tidlists(m: int, n: int, p: float, seed: int, s: int = 0, name: str = "") -> Instance:
-    """Uniform density p for every item (the Bernoulli workloads)."""
-    return from_lists([bernoulli_item(_item_rng(seed, i), m, p) for i in range(n)], m, s, name)
+def _bernoulli_block(args):
+    """Worker: items [a, b) of a Bernoulli instance written into a new
+    shared-memory block; returns (block name, sizes)."""
+    from multiprocessing import shared_memory
+    m, p, seed, a, b = args
+    parts = [bernoulli_item(_item_rng(seed, i), m, p) for i in range(a, b)]
+    total = sum(x.size for x in parts)
+    shm = shared_memory.SharedMemory(create=True, size=max(4 * total, 4))
+    out = np.ndarray((total,), dtype=np.uint32, buffer=shm.buf)
+    pos = 0
+    for x in parts:
+        out[pos:pos + x.size] = x
+        pos += x.size
+    name = shm.name
+    shm.close()
+    return name, np.array([x.size for x in parts], dtype=np.int64)
+
+
+def bernoulli_tidlists(m: int, n: int, p: float, seed: int, s: int = 0, name: str = "",
+                       workers: int = 1) -> Instance:
+    """Uniform density p for every item (the Bernoulli workloads).  With
+    workers > 1 the items are generated in spawned processes (safe after CUDA
+    is initialised); every item has its own stream, so the result is the same."""
+    if workers <= 1 or n < 2 * workers:
+        return from_lists([bernoulli_item(_item_rng(seed, i), m, p) for i in range(n)], m, s, name)
+    import multiprocessing as mp
+    from multiprocessing import shared_memory
+    step = max(1, -(-n // (4 * workers)))
+    jobs = [(m, p, seed, a, min(n, a + step)) for a in range(0, n, step)]
+    sizes = np.zeros(n, dtype=np.int64)
+    blocks = []
+    with mp.get_context("spawn").Pool(workers) as pool:
+        for (_, _, _, a, b), (shm_name, got) in zip(jobs, pool.imap(_bernoulli_block, jobs)):
+            sizes[a:b] = got
+            blocks.append(shm_name)
+    offsets = np.zeros(n + 1, dtype=np.uint64)
+    np.cumsum(sizes, out=offsets[1:])
+    tids = np.empty(int(offsets[-1]), dtype=np.uint32)
+    for (_, _, _, a, b), shm_name in zip(jobs, blocks):
+        shm = shared_memory.SharedMemory(name=shm_name)
+        try:
+            cnt = int(offsets[b] - offsets[a])
+            tids[int(offsets[a]):int(offsets[b])] = np.ndarray((cnt,), dtype=np.uint32, buffer=shm.buf)
+        finally:
+            shm.close()
+            shm.unlink()
+    return Instance(m=m, n=n, offsets=offsets, tids=tids, s=s, name=name)
 
 
 def zipf_probabilities(n: int, density: float, exponent: float = 1.0) -> np.ndarray:
@@ -163,12 +207,13 @@ def sorted_u32(count: int, seed: int, max_gap: int = 255) -> np.ndarray:
     return vals.astype(np.uint32)
 
 
-def workload_instance(name: str, scale_n: int | None = None) -> Instance:
-    """Instance of a named workload; `scale_n` truncates the item count."""
+def workload_instance(name: str, scale_n: int | None = None, workers: int = 1) -> Instance:
+    """Instance of a named workload; `scale_n` truncates the item count;
+    `workers` > 1 generates Bernoulli workloads in parallel (same result)."""
     c = WORKLOADS[name]
     n = c["n"] if scale_n is None else min(c["n"], scale_n)
     if c["kind"] == "bernoulli":
-        return bernoulli_tidlists(c["m"], n, c["p"], c["seed"], c["s"], name)
+        return bernoulli_tidlists(c["m"], n, c["p"], c["seed"], c["s"], name, workers=workers)
     return zipf_tidlists(c["m"], n, c["density"], c["seed"], 1.0, c["s"], name)
 
 

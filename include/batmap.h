@@ -314,6 +314,9 @@ typedef struct batmap_out {
  *   outs : host batmap_out[k]; n_out is filled in for each instance.
  * Returns BATMAP_ERR_CAPACITY if any instance overflowed its buffer (that
  * instance's first cap triples are written).  Synchronises the stream.
+ * Afterwards batmap_get_timing of every set of the batch reports the batched
+ * pass: compare_ms = the one compare launch over all instances, compact_ms =
+ * all corrections and compactions, pairs_ms = the whole pass.
  */
 batmap_status pair_support_batch(batmap_set *const *sets, const uint32_t *s, uint32_t k,
                                  batmap_out *outs, cudaStream_t stream);
@@ -433,9 +436,12 @@ batmap_status pair_support_dense(uint32_t m, uint32_t n, const uint64_t *d_offse
  *             BATMAP_ERR_CAPACITY with the first cap triples if cap is short).
  * The first call on a device looks up the device address of the fixed array
  * (once per device, with that device current); make that first call before
- * any stream capture.  All calls share the one array: calls whose work
- * overlaps on the GPU (different streams or threads without ordering) race
- * and must not be issued.  Synchronises the stream.
+ * any stream capture.  With lazy module loading (the CUDA default) that
+ * first lookup is also when the array's memory is reserved on the device, so
+ * a caller that must not see any reservation during its critical section
+ * makes one call beforehand.  All calls share the one array: calls whose
+ * work overlaps on the GPU (different streams or threads without ordering)
+ * race and must not be issued.  Synchronises the stream.
  */
 batmap_status pair_threshold_noalloc(const uint32_t *d_full, uint32_t n, uint32_t s, uint32_t *d_pairs,
                                      uint64_t cap, uint64_t *n_out, cudaStream_t stream);

@@ -466,6 +466,13 @@ def pair_threshold_noalloc(full, n: int, s: int, pairs, stream=None) -> int:
     buffer (cuda int32 [cap, 3]) without any device allocation by the library;
     returns n_out.  For callers that cannot allocate device memory."""
     L = load_library()
+    npairs = int(n) * (int(n) - 1) // 2 if int(n) > 1 else 0
+    if full is not None and full.element_size() != 4:
+        raise ValueError(f"full must hold 4-byte supports, got {full.dtype}")
+    if pairs is not None and pairs.element_size() != 4:
+        raise ValueError(f"pairs must hold 4-byte integers, got {pairs.dtype}")
+    if npairs and (full is None or int(full.numel()) < npairs):
+        raise ValueError(f"full must hold n(n-1)/2 = {npairs} supports for n = {n}")
     n_out = ctypes.c_uint64(0)
     cap = pairs.numel() // 3 if pairs is not None else 0
     rc = L.pair_threshold_noalloc(_ptr(full), int(n), int(s), _ptr(pairs), cap, ctypes.byref(n_out),

@@ -30,6 +30,7 @@ struct BatchPlan {
     cudaStream_t stream = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    PhaseEvents ev;  // recorded by the graph: 0 start, 1 / 2 around the compare, 3 end
     ~BatchPlan() {
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
@@ -56,14 +57,18 @@ static std::vector<uint64_t> plan_key(batmap_set *const *sets, const uint32_t *s
 
 static void enqueue_batch(BatchPlan *P, batmap_set *const *sets, const uint32_t *s, uint32_t k,
                           const batmap_out *outs, cudaStream_t st) {
+    P->ev.record(0, st);
     for (uint32_t q = 0; q < k; q++) {
         const uint64_t np = sets[q]->npairs();
         if (np) BM_CUDA(cudaMemsetAsync(P->C[q], 0, np * sizeof(uint32_t), st));
     }
     BM_CUDA(cudaMemsetAsync(P->d_counter.p, 0, 2 * sizeof(uint32_t), st));
+    P->ev.record(1, st);
     launch_compare(P->d_views.p, P->d_units.p, P->nunits, P->nmain, P->d_counter.p, st);
+    P->ev.record(2, st);
     for (uint32_t q = 0; q < k; q++)
         enqueue_correct_compact(sets[q], P->C[q], s[q], outs[q].d_pairs, outs[q].cap, P->d_totals.p + q, st);
+    P->ev.record(3, st);
 }
 
 static BatchPlan *make_plan(batmap_set *const *sets, const uint32_t *s, uint32_t k, const batmap_out *outs,
@@ -103,6 +108,7 @@ static BatchPlan *make_plan(batmap_set *const *sets, const uint32_t *s, uint32_t
                                 cudaMemcpyHostToDevice, st));
     BM_CUDA(cudaStreamSynchronize(st));
     prepare_compare();
+    P->ev.create();
 
     // capture the whole batch (zeroing, one compare launch, k compactions)
     cudaStream_t cap_st = st;
@@ -149,10 +155,16 @@ void run_batch(batmap_set *const *sets, const uint32_t *s, uint32_t k, batmap_ou
     std::vector<uint64_t> totals(k);
     BM_CUDA(cudaMemcpyAsync(totals.data(), P->d_totals.p, k * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
     BM_CUDA(cudaStreamSynchronize(st));
+    // every set of the batch reports the batched pass: the one compare launch
+    // over all instances and the corrections + compactions after it
+    const float cmp = P->ev.ms(1, 2), cc = P->ev.ms(2, 3), all = P->ev.ms(0, 3);
     bool overflow = false;
     for (uint32_t q = 0; q < k; q++) {
         outs[q].n_out = totals[q];
         overflow |= totals[q] > outs[q].cap;
+        sets[q]->timing.compare_ms = cmp;
+        sets[q]->timing.compact_ms = cc;
+        sets[q]->timing.pairs_ms = all;
     }
     if (overflow) throw Error{BATMAP_ERR_CAPACITY, "an instance's d_pairs is too small (see n_out)"};
 }

@@ -107,24 +107,37 @@ void enqueue_correct_compact(batmap_set *S, uint32_t *C, uint32_t s, uint32_t *d
     }
 }
 
-// Threshold compaction of a packed support triangle that no set owns (the
-// dense path); block counts live in the caller's buffer.
-void enqueue_threshold(uint32_t *C, uint64_t n, uint32_t s, uint32_t *d_pairs, uint64_t cap,
-                       DevBuf<uint64_t> *blocksums, uint64_t *d_total, cudaStream_t st) {
+// Number of block counts the threshold compaction of n items needs.
+uint64_t threshold_blocks(uint64_t n) {
+    const uint64_t npairs = n * (n > 0 ? n - 1 : 0) / 2;
+    return (npairs + CCHUNK - 1) / CCHUNK;
+}
+
+// Threshold compaction of a packed support triangle that no set owns, with
+// block counts in blocksums[0 .. threshold_blocks(n)) provided by the caller;
+// allocates nothing.
+void enqueue_threshold_into(const uint32_t *C, uint64_t n, uint32_t s, uint32_t *d_pairs, uint64_t cap,
+                            uint64_t *blocksums, uint64_t *d_total, cudaStream_t st) {
     const uint64_t npairs = n * (n > 0 ? n - 1 : 0) / 2;
     if (npairs == 0) {
         BM_CUDA(cudaMemsetAsync(d_total, 0, sizeof(uint64_t), st));
         return;
     }
-    const uint64_t nblk = (npairs + CCHUNK - 1) / CCHUNK;
-    blocksums->ensure(nblk + 1);
-    k_threshold<false><<<(unsigned)nblk, CTPB, 0, st>>>(C, npairs, n, 0, s, blocksums->p, nullptr, 0);
+    const uint64_t nblk = threshold_blocks(n);
+    k_threshold<false><<<(unsigned)nblk, CTPB, 0, st>>>(C, npairs, n, 0, s, blocksums, nullptr, 0);
     BM_CHECK_LAUNCH();
-    scan_exclusive(blocksums->p, nblk, d_total, st);
+    scan_exclusive(blocksums, nblk, d_total, st);
     if (cap && d_pairs) {
-        k_threshold<true><<<(unsigned)nblk, CTPB, 0, st>>>(C, npairs, n, 0, s, blocksums->p, d_pairs, cap);
+        k_threshold<true><<<(unsigned)nblk, CTPB, 0, st>>>(C, npairs, n, 0, s, blocksums, d_pairs, cap);
         BM_CHECK_LAUNCH();
     }
+}
+
+// The same for the dense path, block counts in a buffer the library grows.
+void enqueue_threshold(const uint32_t *C, uint64_t n, uint32_t s, uint32_t *d_pairs, uint64_t cap,
+                       DevBuf<uint64_t> *blocksums, uint64_t *d_total, cudaStream_t st) {
+    blocksums->ensure(threshold_blocks(n) + 1);
+    enqueue_threshold_into(C, n, s, d_pairs, cap, blocksums->p, d_total, st);
 }
 
 }  // namespace bm

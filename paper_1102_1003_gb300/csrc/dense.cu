@@ -36,7 +36,7 @@
 
 namespace bm {
 
-void enqueue_threshold(uint32_t *C, uint64_t n, uint32_t s, uint32_t *d_pairs, uint64_t cap,
+void enqueue_threshold(const uint32_t *C, uint64_t n, uint32_t s, uint32_t *d_pairs, uint64_t cap,
                        DevBuf<uint64_t> *blocksums, uint64_t *d_total, cudaStream_t st);
 
 namespace dense {

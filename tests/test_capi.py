@@ -123,3 +123,19 @@ def test_binding_refuses_a_second_device(monkeypatch):
     current["dev"] = 1
     with pytest.raises(ValueError, match="one GPU per process"):
         batmap._ptr(FakeCuda(1))          # a second GPU in the same process
+
+
+def test_noalloc_wrapper_refuses_wrong_buffers():
+    """The binding refuses supports or pair buffers of the wrong element size
+    and a support array shorter than n(n-1)/2 before any call reaches the GPU."""
+    torch = pytest.importorskip("torch")
+    import paper_1102_1003_gb300 as pkg
+    pairs = torch.zeros((4, 3), dtype=torch.int32)
+    with pytest.raises(ValueError):
+        pkg.pair_threshold_noalloc(torch.zeros(45, dtype=torch.int64), 10, 1, pairs)
+    with pytest.raises(ValueError):
+        pkg.pair_threshold_noalloc(torch.zeros(44, dtype=torch.int32), 10, 1, pairs)
+    with pytest.raises(ValueError):
+        pkg.pair_threshold_noalloc(torch.zeros(45, dtype=torch.int32), 10, 1, torch.zeros((4, 3), dtype=torch.int16))
+    with pytest.raises(ValueError):
+        pkg.pair_threshold_noalloc(None, 10, 1, pairs)

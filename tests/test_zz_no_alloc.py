@@ -56,3 +56,44 @@ def test_noalloc_matches_pair_support_all_twice():
     rc = B.load_library().pair_threshold_noalloc(None, 30_000, 1, None, 0, ctypes.byref(n_out), None)
     assert rc == pkg.BATMAP_ERR_CAPACITY
     assert b"2^28" in B.load_library().batmap_last_error()
+
+
+def _numpy_compaction(full: np.ndarray, n: int, s: int) -> np.ndarray:
+    """(i, j, support) of the packed supports >= s, in array order (= lexicographic)."""
+    idx = np.flatnonzero(full >= s).astype(np.int64)
+    rows = np.arange(n, dtype=np.int64)
+    starts = rows * n - rows * (rows + 1) // 2
+    i = np.searchsorted(starts, idx, side="right") - 1
+    j = idx - starts[i] + i + 1
+    return np.stack([i, j, full[idx].astype(np.int64)], axis=1).astype(np.uint32)
+
+
+@pytest.mark.parametrize("n", [5_000, 23_170])
+def test_noalloc_random_supports_many_tiles_and_capacity_edge(n):
+    """Random supports: n = 5,000 needs more than one tile of the single-block
+    scan (3,052 block counts); n = 23,170 is the largest accepted size
+    (n(n-1)/2 <= 2^28).  Two calls in a row, against a numpy compaction."""
+    import torch
+    import paper_1102_1003_gb300 as pkg
+    npairs = n * (n - 1) // 2
+    rng = np.random.default_rng(n)
+    host = rng.integers(0, 1 << 20, npairs, dtype=np.uint32)
+    s = (1 << 20) - 1500
+    want = _numpy_compaction(host, n, s)
+    full = torch.from_numpy(host.view(np.int32)).to("cuda")
+    del host
+    for call in range(2):
+        out = torch.full((want.shape[0] + 3, 3), -1, dtype=torch.int32, device="cuda")
+        n_out = pkg.pair_threshold_noalloc(full, n, s, out)
+        assert n_out == want.shape[0], call
+        got = out.cpu().numpy()
+        assert np.array_equal(got[:n_out].astype(np.uint32), want), call
+        assert (got[n_out:] == -1).all()
+
+
+def test_noalloc_refuses_one_item_beyond_the_fixed_array():
+    from paper_1102_1003_gb300 import batmap as B
+    import paper_1102_1003_gb300 as pkg
+    n_out = ctypes.c_uint64(0)
+    rc = B.load_library().pair_threshold_noalloc(None, 23_171, 1, None, 0, ctypes.byref(n_out), None)
+    assert rc == pkg.BATMAP_ERR_CAPACITY
