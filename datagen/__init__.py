@@ -336,6 +336,26 @@ def pool_blocks(count: int, universe: int, lo: int, hi: int, seed: int, workers:
                 shm.unlink()
 
 
+def _pool_sets_job(args):
+    universe, seed, pairs = args
+    return [pool_set(universe, int(k), seed, int(i)) for i, k in pairs]
+
+
+def pool_subset(universe: int, lo: int, hi: int, seed: int, count: int, ids, workers: int = 8) -> Instance:
+    """The pool sets `ids` (in that order) of the pool pool_blocks / pool_tidlists
+    generate, regenerated in spawned worker processes: the same sets, without
+    generating the rest of the pool."""
+    import multiprocessing as mp
+    sizes = pool_sizes(count, lo, hi, seed)
+    ids = [int(i) for i in ids]
+    pairs = [(i, int(sizes[i])) for i in ids]
+    step = max(1, -(-len(pairs) // (4 * max(workers, 1))))
+    jobs = [(universe, seed, pairs[a:a + step]) for a in range(0, len(pairs), step)]
+    with mp.get_context("spawn").Pool(max(workers, 1)) as pool:
+        lists = [x for part in pool.map(_pool_sets_job, jobs) for x in part]
+    return from_lists(lists, universe, 0, "pool_subset")
+
+
 def pool_tidlists(count: int, universe: int, lo: int, hi: int, seed: int) -> Instance:
     """Serving pool: `count` sets over [0, universe) with Zipf sizes, uniform members."""
     sizes = pool_sizes(count, lo, hi, seed)

@@ -70,6 +70,19 @@ typedef int batmap_status;
  *       violation returns BATMAP_ERR_ARG.  Default 1.
  *   shape_mask : bit s-1 allows compare tile shape s (1..16) when tile is 0;
  *       0 allows every shape.  Default 0.
+ *   reserved : must be 0.
+ *   perm_seed : seed of the permutations pi_t that the library computes when
+ *       a build is given no permutation table (d_perm = NULL).  Sec. III-A
+ *       draws pi_1..pi_3 at random without fixing a generator; the library's
+ *       pi_t (t = 0, 1, 2, and 3 for 3-of-4 sets) is defined as follows.
+ *       Round keys: SplitMix64 (Steele, Lea, Flood 2014) started from the
+ *       seed; table t takes outputs 4t .. 4t+3, low 32 bits each.  One pass
+ *       E_t: a four-round balanced Feistel network on b bits, b the smallest
+ *       even number >= max(2, ceil(log2 m)), halves of b/2 bits, each round
+ *       (L, R) -> (R, L xor (fmix32(R xor k) mod 2^(b/2))) with fmix32 the
+ *       32-bit finalizer of MurmurHash3.  pi_t(x): E_t applied to x until the
+ *       value is below m (cycle walking).  Computed in the kernels; no table
+ *       is stored.  Default 1.
  */
 typedef struct batmap_params {
     uint32_t load_num;
@@ -79,6 +92,8 @@ typedef struct batmap_params {
     uint32_t tile;
     uint32_t validate;
     uint32_t shape_mask;
+    uint32_t reserved;
+    uint64_t perm_seed;
 } batmap_params;
 
 /* Opaque handle to n BatMaps built from one instance (owned by the library). */
@@ -125,7 +140,8 @@ const char *batmap_last_error(void);
  *   d_offsets : device uint64[n+1], CSR offsets.
  *   d_tids    : device uint32[offsets[n]], CSR tids (may be NULL when empty).
  *   d_perm    : device uint32[3*m]; row t (t = 0, 1, 2) is the permutation
- *               pi_{t+1} of [0, m) used by the layout hash.
+ *               pi_{t+1} of [0, m) used by the layout hash; or NULL for the
+ *               permutations the library computes from p->perm_seed.
  *   stream    : CUDA stream for all work of this call.
  *   out       : receives the new handle; release it with batmap_free.
  * The call synchronises the stream (sizes are needed on the host).  The
@@ -161,7 +177,8 @@ batmap_status batmap_build_cross(const batmap_params *p, uint32_t m, uint32_t n_
  *   smallest shift >= min_shift with m <= 63 * 2^s; elements left with fewer
  *   than three copies are failed insertions (F_i), corrected exactly.
  *   d_perm : device uint32[(d+1) * m], rows pi_0 .. pi_d (the library keeps a
- *            copy for d = 3).  Other arguments as batmap_build.
+ *            copy for d = 3), or NULL for the computed permutations of
+ *            p->perm_seed (rows t = 0 .. d).  Other arguments as batmap_build.
  * Items keep their original order (no width sort); h_bytes of
  * batmap_export_layout follow it.  Errors: BATMAP_ERR_ARG for d outside
  * {2, 3} or invalid input.
@@ -249,7 +266,8 @@ batmap_status pair_support_all(batmap_set *set, uint32_t s, uint32_t *d_pairs, u
  * the CSR tidlists and permutations to the device, builds the BatMaps, counts
  * all pairs, and copies the frequent pairs back.
  *   h_offsets, h_tids, h_perm : host inputs as in batmap_build (pinned
- *       memory gives the fastest copies).
+ *       memory gives the fastest copies); h_perm may be NULL (computed
+ *       permutations, nothing to copy).
  *   h_pairs, cap, n_out : host output triples as in pair_support_all.
  * Synchronises the stream; device memory is released before returning.
  */
@@ -330,8 +348,10 @@ typedef struct batmap_pool batmap_pool;
  * Build a pool from n sets over the universe [0, m) given as CSR tidlists (as
  * in batmap_build).  Every set keeps a device copy of its sorted tidlist; sets
  * for which the 8-bit BatMap is compact (c |S| >= r_0, Sec. III-A) also get a
- * BatMap built with the same GPU build as batmap_build.  The caller may free
- * its buffers after the call.  Synchronises the stream.
+ * BatMap built with the same GPU build as batmap_build.  d_perm is the
+ * caller's device uint32[3*m] permutation table (copied) or NULL for the
+ * permutations the library computes from p->perm_seed (no table is kept).
+ * The caller may free its buffers after the call.  Synchronises the stream.
  */
 batmap_status batmap_pool_create(const batmap_params *p, uint32_t m, uint32_t n, const uint64_t *d_offsets,
                                  const uint32_t *d_tids, const uint32_t *d_perm, cudaStream_t stream,
@@ -414,6 +434,18 @@ batmap_status batmap_serve(const batmap_pool *pool, const uint32_t *h_qoff, cons
 batmap_status pair_support_dense(uint32_t m, uint32_t n, const uint64_t *d_offsets, const uint32_t *d_tids,
                                  uint32_t s, uint32_t *d_pairs, uint64_t cap, uint64_t *n_out,
                                  uint32_t *d_full, batmap_timing *timing, cudaStream_t stream);
+
+/*
+ * Test hook for the error path of the dense kernel's bounded pipeline waits
+ * (no GPU fault is involved).  The next pair_support_dense call in this
+ * process launches its tensor-core kernel with the TMA producer issuing no
+ * loads and every mbarrier wait limited to spin_limit polls: every consumer
+ * wait gives up while no copy and no MMA is in flight, the kernel frees its
+ * tensor memory and returns, and the call returns BATMAP_ERR_TIMEOUT (its
+ * outputs are unspecified).  The hook applies to one call; spin_limit 0
+ * cancels it.  Later calls run normally.
+ */
+void batmap_test_dense_timeout(uint32_t spin_limit);
 
 /*
  * Frequent pairs from already counted supports, for callers that cannot

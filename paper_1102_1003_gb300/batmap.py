@@ -29,7 +29,7 @@ EXPORTED = [
     "pair_support_batch", "batmap_get_timing", "batmap_kernel_launches", "pair_threshold_noalloc",
     "pair_support_dense", "batmap_pool_create", "batmap_pool_free", "batmap_pool_info", "intersect_query",
     "batmap_serve", "batmap_autotune", "batmap_release_scratch", "intersect_query_list", "batmap_build_cross",
-    "batmap_build_d", "itemset_support", "frequent_triples",
+    "batmap_build_d", "itemset_support", "frequent_triples", "batmap_test_dense_timeout",
 ]
 
 
@@ -37,7 +37,8 @@ class batmap_params(ctypes.Structure):
     _fields_ = [("load_num", ctypes.c_uint32), ("load_den", ctypes.c_uint32),
                 ("max_loop", ctypes.c_uint32), ("min_shift", ctypes.c_uint32),
                 ("tile", ctypes.c_uint32), ("validate", ctypes.c_uint32),
-                ("shape_mask", ctypes.c_uint32)]
+                ("shape_mask", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("perm_seed", ctypes.c_uint64)]
 
 
 class batmap_info(ctypes.Structure):
@@ -155,6 +156,8 @@ def load_library(path: str = LIB_PATH):
     L.itemset_support.restype = ctypes.c_int
     L.frequent_triples.argtypes = [vp, u32, vp, u64, vp, u64, ctypes.POINTER(u64), ctypes.POINTER(u64), vp]
     L.frequent_triples.restype = ctypes.c_int
+    L.batmap_test_dense_timeout.argtypes = [u32]
+    L.batmap_test_dense_timeout.restype = None
     _lib = L
     return L
 
@@ -210,7 +213,8 @@ def _ptr(t):
 
 
 def _check_inputs(offsets, tids, perm=None):
-    """CSR offsets are 8-byte, tids and permutations 4-byte elements (the ABI's uint64 / uint32)."""
+    """CSR offsets are 8-byte, tids and permutations 4-byte elements (the ABI's uint64 / uint32).
+    perm None selects the permutations the library computes (params.perm_seed)."""
     if offsets.element_size() != 8:
         raise ValueError(f"offsets must hold 8-byte integers, got {offsets.dtype}")
     if tids.element_size() != 4:
@@ -248,13 +252,15 @@ class BatMapSet:
         return batmap_get_info(self)
 
 
-def batmap_build(m: int, offsets, tids, perm, params: batmap_params | None = None, stream=None) -> BatMapSet:
+def batmap_build(m: int, offsets, tids, perm=None, params: batmap_params | None = None,
+                 stream=None) -> BatMapSet:
     """Build the BatMaps of n = offsets.numel() - 1 items from device CSR tidlists.
 
     offsets: cuda uint64 (int64) tensor [n+1]; tids: cuda int32/uint32 [T];
-    perm: cuda int32/uint32 [3, m] (three permutations of [0, m))."""
+    perm: cuda int32/uint32 [3, m] (three permutations of [0, m)), or None for the
+    permutations the library computes from params.perm_seed."""
     _check_inputs(offsets, tids, perm)
-    if int(m) >= 1 and int(perm.numel()) != 3 * int(m):
+    if perm is not None and int(m) >= 1 and int(perm.numel()) != 3 * int(m):
         raise ValueError(f"perm must hold 3 rows of m = {m} entries")
     L = load_library()
     n = int(offsets.numel()) - 1
@@ -265,12 +271,12 @@ def batmap_build(m: int, offsets, tids, perm, params: batmap_params | None = Non
     return BatMapSet(h, int(m), n)
 
 
-def batmap_build_cross(m: int, n_a: int, offsets, tids, perm, params: batmap_params | None = None,
+def batmap_build_cross(m: int, n_a: int, offsets, tids, perm=None, params: batmap_params | None = None,
                        stream=None) -> BatMapSet:
     """Cross-mode set: the CSR holds n_a sets of family A then the sets of family B;
     pair_support_all then reports the n_a x n_b supports |A_i cap B_j|."""
     _check_inputs(offsets, tids, perm)
-    if int(m) >= 1 and int(perm.numel()) != 3 * int(m):
+    if perm is not None and int(m) >= 1 and int(perm.numel()) != 3 * int(m):
         raise ValueError(f"perm must hold 3 rows of m = {m} entries")
     L = load_library()
     n = int(offsets.numel()) - 1
@@ -284,14 +290,15 @@ def batmap_build_cross(m: int, n_a: int, offsets, tids, perm, params: batmap_par
     return b
 
 
-def batmap_build_d(d: int, m: int, offsets, tids, perm, params: batmap_params | None = None,
+def batmap_build_d(d: int, m: int, offsets, tids, perm=None, params: batmap_params | None = None,
                    stream=None) -> BatMapSet:
     """d-of-(d+1) BatMaps (Sec. V generalisation): d = 2 is batmap_build; d = 3 builds
-    3-of-4 BatMaps for itemset_support / frequent_triples.  perm: cuda [d+1, m]."""
+    3-of-4 BatMaps for itemset_support / frequent_triples.  perm: cuda [d+1, m] or None
+    (computed from params.perm_seed)."""
     _check_inputs(offsets, tids, perm)
     L = load_library()
     n = int(offsets.numel()) - 1
-    if d in (2, 3) and int(m) >= 1 and int(perm.numel()) != (d + 1) * int(m):
+    if perm is not None and d in (2, 3) and int(m) >= 1 and int(perm.numel()) != (d + 1) * int(m):
         raise ValueError(f"perm must hold {d + 1} rows of m = {m} entries")
     h = ctypes.c_void_p()
     pp = ctypes.byref(params) if params is not None else None
@@ -419,6 +426,12 @@ def pair_support_dense(m: int, offsets, tids, s: int, pairs=None, full=None, str
     return int(n_out.value), pairs.view(-1, 3)[:k], t.as_dict()
 
 
+def batmap_test_dense_timeout(spin_limit: int):
+    """Make the next pair_support_dense call exercise its bounded-wait error path
+    (producer issues nothing, waits give up after spin_limit polls); 0 cancels."""
+    load_library().batmap_test_dense_timeout(int(spin_limit))
+
+
 def batmap_autotune(sets, stream=None):
     """Measure every tile shape on these sets, adopt the result for scheduling and
     reschedule them; returns the relative throughput per shape (1..16)."""
@@ -447,15 +460,17 @@ def pair_support_batch(sets, s_list, pairs_list, full_list=None, stream=None):
     return [int(outs[q].n_out) for q in range(k)]
 
 
-def pair_support_host(m: int, offsets: np.ndarray, tids: np.ndarray, perm: np.ndarray, s: int,
+def pair_support_host(m: int, offsets: np.ndarray, tids: np.ndarray, perm, s: int,
                       pairs_out: np.ndarray, params: batmap_params | None = None, stream=None) -> int:
-    """End to end from host (preferably pinned) numpy buffers; returns n_out."""
+    """End to end from host (preferably pinned) numpy buffers; returns n_out.  perm None
+    selects the computed permutations (nothing to copy)."""
     L = load_library()
     n = offsets.size - 1
     n_out = ctypes.c_uint64(0)
     pp = ctypes.byref(params) if params is not None else None
     rc = L.pair_support_host(pp, int(m), n, offsets.ctypes.data, tids.ctypes.data if tids.size else None,
-                             perm.ctypes.data, int(s), pairs_out.ctypes.data, pairs_out.size // 3,
+                             perm.ctypes.data if perm is not None else None, int(s), pairs_out.ctypes.data,
+                             pairs_out.size // 3,
                              ctypes.byref(n_out), _stream_handle(stream))
     _check(rc, allow=(BATMAP_ERR_CAPACITY,))
     return int(n_out.value)
@@ -502,9 +517,11 @@ class BatMapPool:
         return {"n_batmaps": nb.value, "batmap_bytes": by.value, "n_elements": ne.value}
 
 
-def batmap_pool_create(m: int, offsets, tids, perm, params: batmap_params | None = None, stream=None) -> BatMapPool:
+def batmap_pool_create(m: int, offsets, tids, perm=None, params: batmap_params | None = None,
+                       stream=None) -> BatMapPool:
+    """Resident pool of sets; perm None selects the computed permutations."""
     _check_inputs(offsets, tids, perm)
-    if int(m) >= 1 and int(perm.numel()) != 3 * int(m):
+    if perm is not None and int(m) >= 1 and int(perm.numel()) != 3 * int(m):
         raise ValueError(f"perm must hold 3 rows of m = {m} entries")
     L = load_library()
     n = int(offsets.numel()) - 1

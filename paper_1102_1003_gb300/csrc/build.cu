@@ -16,6 +16,7 @@
 
 #include "common.cuh"
 #include "items.cuh"
+#include "perm.cuh"
 #include "scan.cuh"
 
 namespace bm {
@@ -63,8 +64,9 @@ __global__ void k_validate_perm(const uint32_t *perm, uint32_t m, uint32_t rows,
 // distinct tables.  Atomic exchanges conserve copies; a chain that exceeds
 // 3*MaxLoop moves drops the copy it holds, and finalize then reports that
 // element as a failed insertion.
-__global__ void k_place(ItemView v, const uint32_t *__restrict__ perm, uint32_t m,
-                        uint32_t shift, uint32_t max_moves, uint32_t *__restrict__ table) {
+__global__ void k_place(ItemView v, const PermView P, uint32_t shift, uint32_t max_moves,
+                        uint32_t *__restrict__ table) {
+    const uint32_t m = P.m;
     uint32_t item;
     uint64_t e0, e1;
     chunk_range(v, blockIdx.x >> 1, &item, &e0, &e1);
@@ -76,7 +78,7 @@ __global__ void k_place(ItemView v, const uint32_t *__restrict__ perm, uint32_t 
         if (x >= m) continue;  // rejected by validation; never index past perm
         uint32_t t = copy;
         for (uint32_t mv = 0; mv < max_moves; mv++) {
-            uint32_t pi = __ldg(&perm[(uint64_t)t * m + x]);
+            uint32_t pi = P(t, x);
             uint64_t pos = base + slot_of(t, pi, r, shift);
             uint32_t old = atomicExch(&table[pos], x);
             if (old == EMPTY) break;
@@ -93,13 +95,12 @@ struct Copies {
 };
 
 __device__ __forceinline__ Copies find_copies(uint32_t x, uint64_t base, uint32_t r, uint32_t shift,
-                                              const uint32_t *__restrict__ perm, uint32_t m,
-                                              const uint32_t *__restrict__ table) {
+                                              const PermView &P, const uint32_t *__restrict__ table) {
     Copies c;
     c.has = 0;
 #pragma unroll
     for (uint32_t t = 0; t < 3; t++) {
-        c.pi[t] = __ldg(&perm[(uint64_t)t * m + x]);
+        c.pi[t] = P(t, x);
         c.pos[t] = base + slot_of(t, c.pi[t], r, shift);
         if (table[c.pos[t]] == x) c.has |= 1u << t;
     }
@@ -112,9 +113,9 @@ __device__ __forceinline__ bool two_copies(uint32_t has) { return __popc(has) ==
 // the copy whose twin sits in the cyclic predecessor table (Fig. 3).
 // Also counts the block's failed insertions into blocksums[block] (the count
 // pass of the ordered compaction that lists them).
-__global__ void k_finalize(ItemView v, const uint32_t *__restrict__ perm, uint32_t m,
-                           uint32_t shift, const uint32_t *__restrict__ table,
+__global__ void k_finalize(ItemView v, const PermView P, uint32_t shift, const uint32_t *__restrict__ table,
                            uint8_t *__restrict__ out, uint64_t *__restrict__ blocksums) {
+    const uint32_t m = P.m;
     __shared__ uint32_t s_fail;
     if (threadIdx.x == 0) s_fail = 0;
     __syncthreads();
@@ -127,7 +128,7 @@ __global__ void k_finalize(ItemView v, const uint32_t *__restrict__ perm, uint32
     for (uint64_t e = e0 + threadIdx.x; e < e1; e += TPB) {
         uint32_t x = v.tids[e];
         if (x >= m) continue;
-        Copies c = find_copies(x, base, r, shift, perm, m, table);
+        Copies c = find_copies(x, base, r, shift, P, table);
         if (!two_copies(c.has)) {
             fails++;
             continue;
@@ -152,9 +153,9 @@ __global__ void k_finalize(ItemView v, const uint32_t *__restrict__ perm, uint32
 
 // Rank of each failing element inside its block, in element order.
 template <bool WRITE>
-__global__ void k_failures(ItemView v, const uint32_t *__restrict__ perm, uint32_t m,
-                           uint32_t shift, const uint32_t *__restrict__ table,
+__global__ void k_failures(ItemView v, const PermView P, uint32_t shift, const uint32_t *__restrict__ table,
                            uint64_t *blocksums, uint32_t *f_item, uint32_t *f_tid) {
+    const uint32_t m = P.m;
     uint32_t item;
     uint64_t e0, e1;
     chunk_range(v, blockIdx.x, &item, &e0, &e1);
@@ -168,7 +169,7 @@ __global__ void k_failures(ItemView v, const uint32_t *__restrict__ perm, uint32
         uint32_t x = 0;
         if (e < e1) {
             x = v.tids[e];
-            fail = x < m && !two_copies(find_copies(x, base, r, shift, perm, m, table).has);
+            fail = x < m && !two_copies(find_copies(x, base, r, shift, P, table).has);
         }
         uint64_t tot;
         uint64_t rank = block_exclusive_scan(fail ? 1 : 0, &tot);
@@ -268,6 +269,30 @@ __global__ void k_corrections(ItemView v, uint32_t m, const uint32_t *bits, cons
 
 // ---- host side -------------------------------------------------------------------
 
+PermView make_perm_view(const uint32_t *table, uint32_t m, uint64_t seed) {
+    PermView P{};
+    P.table = table;
+    P.m = m;
+    uint32_t b = 0;
+    while (b < 32 && (1ull << b) < (uint64_t)m) b++;  // ceil(log2 m)
+    b = std::max<uint32_t>(b, 2);
+    b += b & 1u;
+    P.half = b / 2;
+    P.mask = (1u << P.half) - 1u;
+    // SplitMix64 from the seed: four round keys per table, low 32 bits each
+    uint64_t state = seed;
+    uint32_t k[4 * PERM_MAX_TABLES];
+    for (int j = 0; j < 4 * PERM_MAX_TABLES; j++) {
+        state += 0x9E3779B97F4A7C15ull;
+        uint64_t z = state;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        k[j] = (uint32_t)(z ^ (z >> 31));
+    }
+    for (int t = 0; t < PERM_MAX_TABLES; t++) P.key[t] = make_uint4(k[4 * t], k[4 * t + 1], k[4 * t + 2], k[4 * t + 3]);
+    return P;
+}
+
 static uint32_t shift_bits(uint32_t m, uint32_t min_shift) {
     uint32_t s = min_shift;
     while ((uint64_t)m > 127ull << s) s++;
@@ -365,7 +390,7 @@ void build_set(batmap_set *S, const uint64_t *d_offsets, const uint32_t *d_tids,
     const uint64_t T = off[n];
     S->n_elements = T;
     BM_REQUIRE(T == 0 || d_tids != nullptr, BATMAP_ERR_ARG, "d_tids is NULL");
-    BM_REQUIRE(m == 0 || d_perm != nullptr || T == 0, BATMAP_ERR_ARG, "d_perm is NULL");
+    const PermView PV = make_perm_view(d_perm, m, P.perm_seed);
 
     // ---- sizes (Sec. III-A) and width-sorted order (Sec. III-C) ----
     S->shift = shift_bits(m, P.min_shift);
@@ -469,13 +494,15 @@ void build_set(batmap_set *S, const uint64_t *d_offsets, const uint32_t *d_tids,
     // ---- validation ----
     if (P.validate) {
         DevBuf<int> d_err(1);
-        DevBuf<uint32_t> d_bits(3ull * ((m + 31) / 32));
+        DevBuf<uint32_t> d_bits(d_perm ? 3ull * ((m + 31) / 32) : 0);
         BM_CUDA(cudaMemsetAsync(d_err.p, 0, sizeof(int), st));
-        BM_CUDA(cudaMemsetAsync(d_bits.p, 0, d_bits.bytes(), st));
+        if (d_perm) BM_CUDA(cudaMemsetAsync(d_bits.p, 0, d_bits.bytes(), st));
         k_validate_tids<<<nch, TPB, 0, st>>>(v, m, d_err.p);
         BM_CHECK_LAUNCH();
-        k_validate_perm<<<grid_for(3ull * m), 256, 0, st>>>(d_perm, m, 3, d_bits.p, d_err.p);
-        BM_CHECK_LAUNCH();
+        if (d_perm) {  // computed permutations are bijections by construction
+            k_validate_perm<<<grid_for(3ull * m), 256, 0, st>>>(d_perm, m, 3, d_bits.p, d_err.p);
+            BM_CHECK_LAUNCH();
+        }
         int err = 0;
         BM_CUDA(cudaMemcpyAsync(&err, d_err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
         BM_CUDA(cudaStreamSynchronize(st));
@@ -489,12 +516,12 @@ void build_set(batmap_set *S, const uint64_t *d_offsets, const uint32_t *d_tids,
         BM_CUDA(cudaMemsetAsync(table.p, 0xFF, S->bytes * sizeof(uint32_t), st));
         const uint32_t max_moves = 3u * std::max<uint32_t>(P.max_loop, 1u);
         E.record(2, st);
-        k_place<<<2u * nch, TPB, 0, st>>>(v, d_perm, m, S->shift, max_moves, table.p);
+        k_place<<<2u * nch, TPB, 0, st>>>(v, PV, S->shift, max_moves, table.p);
         BM_CHECK_LAUNCH();
         E.record(3, st);
         // failed insertions, ordered by (item, tid): counted by finalize, listed below
         DevBuf<uint64_t> bs(nch + 1), d_tot(1);
-        k_finalize<<<nch, TPB, 0, st>>>(v, d_perm, m, S->shift, table.p, S->d_bm.p, bs.p);
+        k_finalize<<<nch, TPB, 0, st>>>(v, PV, S->shift, table.p, S->d_bm.p, bs.p);
         BM_CHECK_LAUNCH();
         k_scan_single_block<<<1, SCAN_TPB, 0, st>>>(bs.p, nch, d_tot.p, 1);
         BM_CHECK_LAUNCH();
@@ -505,7 +532,7 @@ void build_set(batmap_set *S, const uint64_t *d_offsets, const uint32_t *d_tids,
         DevBuf<uint32_t> f_item(nfail);
         S->d_fail_tid.alloc(nfail);
         if (nfail) {
-            k_failures<true><<<nch, TPB, 0, st>>>(v, d_perm, m, S->shift, table.p, bs.p, f_item.p,
+            k_failures<true><<<nch, TPB, 0, st>>>(v, PV, S->shift, table.p, bs.p, f_item.p,
                                                   S->d_fail_tid.p);
             BM_CHECK_LAUNCH();
         }

@@ -76,6 +76,8 @@ void batmap_default_params(batmap_params *p) {
     p->tile = 0;
     p->validate = 1;
     p->shape_mask = 0;
+    p->reserved = 0;
+    p->perm_seed = 1;
 }
 
 const char *batmap_last_error(void) { return g_last_error.c_str(); }
@@ -250,7 +252,7 @@ batmap_status pair_support_host(const batmap_params *p, uint32_t m, uint32_t n, 
         BM_REQUIRE(cap == 0 || h_pairs, BATMAP_ERR_ARG, "h_pairs is NULL with cap > 0");
         const uint64_t T = h_offsets[n];
         DevBuf<uint64_t> d_off(n + 1);
-        DevBuf<uint32_t> d_tids(T), d_perm(3ull * m), d_pairs(3 * cap);
+        DevBuf<uint32_t> d_tids(T), d_perm(h_perm ? 3ull * m : 0), d_pairs(3 * cap);
         BM_CUDA(cudaMemcpyAsync(d_off.p, h_offsets, (n + 1) * 8ull, cudaMemcpyHostToDevice, st));
         if (T) BM_CUDA(cudaMemcpyAsync(d_tids.p, h_tids, T * 4ull, cudaMemcpyHostToDevice, st));
         if (h_perm) BM_CUDA(cudaMemcpyAsync(d_perm.p, h_perm, 3ull * m * 4, cudaMemcpyHostToDevice, st));

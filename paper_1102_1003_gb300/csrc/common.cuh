@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "batmap.h"
+#include "perm.cuh"
 
 namespace bm {
 
@@ -213,7 +214,8 @@ struct batmap_set {
     // 3-of-4 sets (original item order): byte offsets, log2 r_i, own copy of pi_0..pi_3
     bm::DevBuf<uint64_t> d_base;          // [n+1]
     bm::DevBuf<uint32_t> d_rlog;          // [n]
-    bm::DevBuf<uint32_t> d_perm;          // [4 m]
+    bm::DevBuf<uint32_t> d_perm;          // [4 m] copy of the caller's table, if one was given
+    bm::PermView perm{};                  // the set's pi_t (table view or computed)
 
     // timing of the most recent calls
     bm::PhaseEvents build_ev, pairs_ev;

@@ -24,10 +24,13 @@
 //
 // Every mbarrier wait is bounded; on timeout the kernel records an error
 // flag, stops issuing work, waits (bounded) for what it issued, frees its
-// tensor memory and returns.
+// tensor memory and returns.  A test hook (batmap_test_dense_timeout) runs
+// one launch whose producer issues no loads and whose waits are short, so
+// that every wait gives up with nothing in flight.
 #include <cuda.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <mutex>
 
@@ -66,9 +69,10 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
-// Bounded wait for the phase with the given parity; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    for (uint32_t it = 0; it < SPIN_LIMIT; it++) {
+// Bounded wait for the phase with the given parity (at most `limit` polls);
+// false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t limit) {
+    for (uint32_t it = 0; it < limit; it++) {
         uint32_t done;
         asm volatile(
             "{\n.reg .pred p;\n"
@@ -138,7 +142,7 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 __global__ void __launch_bounds__(THREADS, 1)
 k_dense_mmt(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
             const Tile *__restrict__ tiles, uint32_t ksplit, uint32_t kblocks, uint32_t n,
-            uint32_t *__restrict__ C, int *__restrict__ err) {
+            uint32_t *__restrict__ C, int *__restrict__ err, uint32_t spin, uint32_t no_loads) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *bits = smem + STAGES * STAGE_BYTES;
@@ -173,11 +177,11 @@ k_dense_mmt(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 0 && lane == 0) {
-        // TMA producer of the packed bits
+        // TMA producer of the packed bits (no_loads: the timeout test issues nothing)
         uint32_t it = 0;
-        for (; it < nk && !s_abort; it++) {
+        for (; it < nk && !s_abort && !no_loads; it++) {
             const uint32_t sb = it % SB, ph = it / SB;
-            if (ph > 0 && !mbar_wait(smem_addr(&bars[BE + sb]), (ph - 1) & 1)) {
+            if (ph > 0 && !mbar_wait(smem_addr(&bars[BE + sb]), (ph - 1) & 1, spin)) {
                 atomicExch(err, 1);
                 s_abort = 1;
                 break;
@@ -194,14 +198,14 @@ k_dense_mmt(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             // wait (bounded) for the last load issued into every bits stage
             for (uint32_t sb = 0; sb < (uint32_t)SB && sb < it; sb++) {
                 const uint32_t last = sb + SB * ((it - 1 - sb) / SB);
-                mbar_wait(smem_addr(&bars[BF + sb]), (last / SB) & 1);
+                mbar_wait(smem_addr(&bars[BF + sb]), (last / SB) & 1, spin);
             }
         }
     } else if (warp == 1 && lane == 0) {
         // MMA issuer
         for (uint32_t it = 0; it < nk; it++) {
             const uint32_t st = it % STAGES;
-            if (s_abort || !mbar_wait(smem_addr(&bars[YF + st]), (it / STAGES) & 1)) {
+            if (s_abort || !mbar_wait(smem_addr(&bars[YF + st]), (it / STAGES) & 1, spin)) {
                 atomicExch(err, 1);
                 s_abort = 1;
                 break;
@@ -225,8 +229,8 @@ k_dense_mmt(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         const uint32_t t = (uint32_t)threadIdx.x - 64;
         for (uint32_t it = 0; it < nk; it++) {
             const uint32_t sb = it % SB, st = it % STAGES;
-            bool ok = !s_abort && mbar_wait(smem_addr(&bars[BF + sb]), (it / SB) & 1);
-            if (ok && it >= (uint32_t)STAGES) ok = mbar_wait(smem_addr(&bars[YE + st]), ((it / STAGES) - 1) & 1);
+            bool ok = !s_abort && mbar_wait(smem_addr(&bars[BF + sb]), (it / SB) & 1, spin);
+            if (ok && it >= (uint32_t)STAGES) ok = mbar_wait(smem_addr(&bars[YE + st]), ((it / STAGES) - 1) & 1, spin);
             if (!ok) {
                 atomicExch(err, 1);
                 s_abort = 1;
@@ -258,7 +262,7 @@ k_dense_mmt(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             // epilogue: TMEM lanes 32*(warp % 4) .. +31 hold tile rows of that quarter
             const uint32_t q = warp & 3;
             bool ready = false;
-            for (int rep = 0; rep < 16 && !ready; rep++) ready = mbar_wait(smem_addr(&bars[ACC]), 0);
+            for (int rep = 0; rep < 16 && !ready; rep++) ready = mbar_wait(smem_addr(&bars[ACC]), 0, spin);
             if (!ready) {
                 atomicExch(err, 1);
                 s_abort = 1;
@@ -371,6 +375,9 @@ struct DenseWork {
 
 static std::mutex g_dense_mu;
 static DenseWork *g_dense = nullptr;
+static std::atomic<uint32_t> g_dense_timeout_test{0};  // one-shot spin limit of the timeout test
+
+void set_dense_timeout_test(uint32_t spin_limit) { g_dense_timeout_test.store(spin_limit); }
 
 void release_dense_workspace() {
     std::lock_guard<std::mutex> lock(g_dense_mu);
@@ -445,8 +452,10 @@ void run_dense(uint32_t m, uint32_t n, const uint64_t *d_off, const uint32_t *d_
             BM_CUDA(cudaFuncSetAttribute(k_dense_mmt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM));
             attr = true;
         }
-        k_dense_mmt<<<(unsigned)(tl.size() * ksplit), THREADS, SMEM, st>>>(mA, mB, W.tiles.p, ksplit, kblocks, n, C,
-                                                                           W.err.p);
+        const uint32_t test_spin = g_dense_timeout_test.exchange(0);
+        k_dense_mmt<<<(unsigned)(tl.size() * ksplit), THREADS, SMEM, st>>>(
+            mA, mB, W.tiles.p, ksplit, kblocks, n, C, W.err.p, test_spin ? test_spin : SPIN_LIMIT,
+            test_spin ? 1u : 0u);
         BM_CHECK_LAUNCH();
     }
     W.ev.record(2, st);
@@ -472,6 +481,8 @@ void run_dense(uint32_t m, uint32_t n, const uint64_t *d_off, const uint32_t *d_
 }
 
 }  // namespace bm
+
+extern "C" void batmap_test_dense_timeout(uint32_t spin_limit) { bm::set_dense_timeout_test(spin_limit); }
 
 extern "C" batmap_status pair_support_dense(uint32_t m, uint32_t n, const uint64_t *d_offsets, const uint32_t *d_tids,
                                             uint32_t s, uint32_t *d_pairs, uint64_t cap, uint64_t *n_out,

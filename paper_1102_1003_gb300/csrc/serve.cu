@@ -21,6 +21,7 @@
 #include <thread>
 
 #include "common.cuh"
+#include "perm.cuh"
 #include "scan.cuh"
 
 namespace bm {
@@ -43,7 +44,7 @@ struct ProbeTask {
 struct PoolView {
     const uint64_t *off;      // [n+1] CSR of all sets
     const uint32_t *tids;
-    const uint32_t *perm;     // [3*m]
+    PermView perm;            // pi_0 .. pi_2 (the caller's table or computed)
     const int32_t *bm_index;  // [n] index among BatMap-backed sets or -1
     const uint64_t *bm_base;  // [nb] byte offset of the BatMap
     const uint32_t *bm_rlog;  // [nb] log2 r
@@ -70,7 +71,7 @@ __device__ __forceinline__ bool member(const PoolView &P, uint32_t c, uint32_t x
     const uint32_t r = 1u << P.bm_rlog[b];
 #pragma unroll
     for (uint32_t t = 0; t < 2; t++) {
-        const uint32_t pi = __ldg(&P.perm[(uint64_t)t * P.m + x]);
+        const uint32_t pi = P.perm(t, x);
         const uint8_t byte = P.bm[base + slot_of(t, pi, r, P.shift)];
         if ((uint32_t)(byte & 0x7F) == (pi >> P.shift) + 1u) return true;
     }
@@ -196,7 +197,6 @@ static void pool_create(const batmap_params *p, uint32_t m, uint32_t n, const ui
                         const uint32_t *d_tids, const uint32_t *d_perm, cudaStream_t st, batmap_pool **out) {
     BM_REQUIRE(out, BATMAP_ERR_ARG, "out is NULL");
     BM_REQUIRE(m >= 1 && m <= (1u << 30), BATMAP_ERR_ARG, "m must be in [1, 2^30]");
-    BM_REQUIRE(d_perm, BATMAP_ERR_ARG, "d_perm is NULL");
     batmap_params P;
     batmap_default_params(&P);
     if (p) P = *p;
@@ -212,10 +212,10 @@ static void pool_create(const batmap_params *p, uint32_t m, uint32_t n, const ui
     const uint64_t T = pool->h_off[n];
     pool->d_off.alloc(n + 1);
     pool->d_tids.alloc(T);
-    pool->d_perm.alloc(3ull * m);
+    if (d_perm) pool->d_perm.alloc(3ull * m);  // computed permutations need no table
     if (n) BM_CUDA(cudaMemcpyAsync(pool->d_off.p, d_offsets, (n + 1) * 8ull, cudaMemcpyDeviceToDevice, st));
     if (T) BM_CUDA(cudaMemcpyAsync(pool->d_tids.p, d_tids, T * 4ull, cudaMemcpyDeviceToDevice, st));
-    BM_CUDA(cudaMemcpyAsync(pool->d_perm.p, d_perm, 3ull * m * 4, cudaMemcpyDeviceToDevice, st));
+    if (d_perm) BM_CUDA(cudaMemcpyAsync(pool->d_perm.p, d_perm, 3ull * m * 4, cudaMemcpyDeviceToDevice, st));
     if (n) {
         DevBuf<int> err(1);
         BM_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
@@ -289,7 +289,7 @@ static void pool_create(const batmap_params *p, uint32_t m, uint32_t n, const ui
             S.n = cn;
             S.stream = st;
             S.skip_schedule = true;
-            build_set(&S, s_off.p, s_tids.p, d_perm);
+            build_set(&S, s_off.p, s_tids.p, d_perm ? pool->d_perm.p : nullptr);
             pool->shift = S.shift;
             BM_CUDA(cudaMemcpyAsync(pool->d_bm.p + bm_pos, S.d_bm.p, S.bytes, cudaMemcpyDeviceToDevice, st));
             std::vector<uint64_t> cf(cn + 1, 0);
@@ -327,7 +327,7 @@ static void pool_create(const batmap_params *p, uint32_t m, uint32_t n, const ui
         BM_CUDA(cudaMemcpyAsync(pool->d_bm_base.p, base.data(), nb * 8ull, cudaMemcpyHostToDevice, st));
         BM_CUDA(cudaMemcpyAsync(pool->d_bm_rlog.p, rlog.data(), nb * 4ull, cudaMemcpyHostToDevice, st));
     }
-    pool->view = PoolView{pool->d_off.p,     pool->d_tids.p,     pool->d_perm.p,
+    pool->view = PoolView{pool->d_off.p,     pool->d_tids.p,     make_perm_view(d_perm ? pool->d_perm.p : nullptr, m, P.perm_seed),
                           pool->d_bm_index.p, pool->d_bm_base.p, pool->d_bm_rlog.p,
                           pool->d_fail_off.p, pool->d_fail_tid.p, pool->d_bm.p,
                           m,                  nb ? pool->shift : shift};

@@ -51,8 +51,9 @@ __device__ __forceinline__ uint32_t code6(uint32_t pi, uint32_t shift) { return 
 // same element leaves the slot unchanged and the element moves on, so copies
 // of one element never share a table.  A chain longer than max_moves drops
 // the copy it holds (the element then fails).
-__global__ void k_place(ItemView v, const uint32_t *__restrict__ perm, uint32_t m, uint32_t shift,
-                        uint32_t max_moves, uint32_t *__restrict__ table) {
+__global__ void k_place(ItemView v, const PermView P, uint32_t shift, uint32_t max_moves,
+                        uint32_t *__restrict__ table) {
+    const uint32_t m = P.m;
     uint32_t item;
     uint64_t e0, e1;
     chunk_range(v, blockIdx.x / COPIES, &item, &e0, &e1);
@@ -64,7 +65,7 @@ __global__ void k_place(ItemView v, const uint32_t *__restrict__ perm, uint32_t 
         if (x >= m) continue;  // rejected by validation; never index past perm
         uint32_t t = copy;
         for (uint32_t mv = 0; mv < max_moves; mv++) {
-            const uint32_t pi = __ldg(&perm[(uint64_t)t * m + x]);
+            const uint32_t pi = P(t, x);
             const uint32_t old = atomicExch(&table[base + slot4(t, pi, r, shift)], x);
             if (old == EMPTY) break;
             x = old;
@@ -80,13 +81,12 @@ struct Copies4 {
 };
 
 __device__ __forceinline__ Copies4 find_copies(uint32_t x, uint64_t base, uint32_t r, uint32_t shift,
-                                               const uint32_t *__restrict__ perm, uint32_t m,
-                                               const uint32_t *__restrict__ table) {
+                                               const PermView &P, const uint32_t *__restrict__ table) {
     Copies4 c;
     c.has = 0;
 #pragma unroll
     for (uint32_t t = 0; t < TABLES; t++) {
-        c.pi[t] = __ldg(&perm[(uint64_t)t * m + x]);
+        c.pi[t] = P(t, x);
         c.pos[t] = base + slot4(t, c.pi[t], r, shift);
         if (table[c.pos[t]] == x) c.has |= 1u << t;
     }
@@ -94,9 +94,9 @@ __device__ __forceinline__ Copies4 find_copies(uint32_t x, uint64_t base, uint32
 }
 
 // Bytes of every element stored three times; failures counted per block.
-__global__ void k_finalize(ItemView v, const uint32_t *__restrict__ perm, uint32_t m, uint32_t shift,
-                           const uint32_t *__restrict__ table, uint8_t *__restrict__ out,
-                           uint64_t *__restrict__ blocksums) {
+__global__ void k_finalize(ItemView v, const PermView P, uint32_t shift, const uint32_t *__restrict__ table,
+                           uint8_t *__restrict__ out, uint64_t *__restrict__ blocksums) {
+    const uint32_t m = P.m;
     __shared__ uint32_t s_fail;
     if (threadIdx.x == 0) s_fail = 0;
     __syncthreads();
@@ -109,7 +109,7 @@ __global__ void k_finalize(ItemView v, const uint32_t *__restrict__ perm, uint32
     for (uint64_t e = e0 + threadIdx.x; e < e1; e += TPB) {
         const uint32_t x = v.tids[e];
         if (x >= m) continue;
-        const Copies4 c = find_copies(x, base, r, shift, perm, m, table);
+        const Copies4 c = find_copies(x, base, r, shift, P, table);
         if (__popc(c.has) != (int)COPIES) {
             fails++;
             continue;
@@ -128,9 +128,9 @@ __global__ void k_finalize(ItemView v, const uint32_t *__restrict__ perm, uint32
 
 // Failed insertions in (item, tid) order: block offsets come from the scan
 // of the finalize counts.
-__global__ void k_failures(ItemView v, const uint32_t *__restrict__ perm, uint32_t m, uint32_t shift,
-                           const uint32_t *__restrict__ table, const uint64_t *blocksums, uint32_t *f_item,
-                           uint32_t *f_tid) {
+__global__ void k_failures(ItemView v, const PermView P, uint32_t shift, const uint32_t *__restrict__ table,
+                           const uint64_t *blocksums, uint32_t *f_item, uint32_t *f_tid) {
+    const uint32_t m = P.m;
     uint32_t item;
     uint64_t e0, e1;
     chunk_range(v, blockIdx.x, &item, &e0, &e1);
@@ -144,7 +144,7 @@ __global__ void k_failures(ItemView v, const uint32_t *__restrict__ perm, uint32
         uint32_t x = 0;
         if (e < e1) {
             x = v.tids[e];
-            fail = x < m && __popc(find_copies(x, base, r, shift, perm, m, table).has) != (int)COPIES;
+            fail = x < m && __popc(find_copies(x, base, r, shift, P, table).has) != (int)COPIES;
         }
         uint64_t tot;
         const uint64_t rank = block_exclusive_scan(fail ? 1 : 0, &tot);
@@ -187,7 +187,6 @@ void build_witness_set(batmap_set *S, const uint64_t *d_offsets, const uint32_t 
     const uint64_t T = off[n];
     S->n_elements = T;
     BM_REQUIRE(T == 0 || d_tids != nullptr, BATMAP_ERR_ARG, "d_tids is NULL");
-    BM_REQUIRE(d_perm != nullptr, BATMAP_ERR_ARG, "d_perm is NULL");
 
     // ---- sizes: four tables of r_i slots; items keep their original order ----
     S->shift = shift_bits63(m, P.min_shift);
@@ -211,12 +210,14 @@ void build_witness_set(batmap_set *S, const uint64_t *d_offsets, const uint32_t 
     S->d_bm.alloc(S->bytes);
     S->d_base.alloc(n + 1);
     S->d_rlog.alloc(n);
-    S->d_perm.alloc((uint64_t)TABLES * m);
+    if (d_perm) S->d_perm.alloc((uint64_t)TABLES * m);  // the caller's table is kept; computed ones need none
     if (n) {
         BM_CUDA(cudaMemcpyAsync(S->d_base.p, base.data(), (n + 1) * 8ull, cudaMemcpyHostToDevice, st));
         BM_CUDA(cudaMemcpyAsync(S->d_rlog.p, rlog.data(), n * 4ull, cudaMemcpyHostToDevice, st));
     }
-    BM_CUDA(cudaMemcpyAsync(S->d_perm.p, d_perm, (uint64_t)TABLES * m * 4, cudaMemcpyDeviceToDevice, st));
+    if (d_perm) BM_CUDA(cudaMemcpyAsync(S->d_perm.p, d_perm, (uint64_t)TABLES * m * 4, cudaMemcpyDeviceToDevice, st));
+    S->perm = make_perm_view(d_perm ? S->d_perm.p : nullptr, m, P.perm_seed);
+    const PermView PV = S->perm;
     if (S->bytes) BM_CUDA(cudaMemsetAsync(S->d_bm.p, 0, S->bytes, st));
     S->d_fail_off.alloc(n + 1);
 
@@ -238,15 +239,17 @@ void build_witness_set(batmap_set *S, const uint64_t *d_offsets, const uint32_t 
 
     if (P.validate) {
         DevBuf<int> d_err(1);
-        DevBuf<uint32_t> d_bits((uint64_t)TABLES * ((m + 31) / 32));
+        DevBuf<uint32_t> d_bits(d_perm ? (uint64_t)TABLES * ((m + 31) / 32) : 0);
         BM_CUDA(cudaMemsetAsync(d_err.p, 0, sizeof(int), st));
-        BM_CUDA(cudaMemsetAsync(d_bits.p, 0, d_bits.bytes(), st));
+        if (d_perm) BM_CUDA(cudaMemsetAsync(d_bits.p, 0, d_bits.bytes(), st));
         if (nch) {
             k_validate_tids<<<nch, TPB, 0, st>>>(v, m, d_err.p);
             BM_CHECK_LAUNCH();
         }
-        k_validate_perm<<<grid_for((uint64_t)TABLES * m), 256, 0, st>>>(d_perm, m, TABLES, d_bits.p, d_err.p);
-        BM_CHECK_LAUNCH();
+        if (d_perm) {  // computed permutations are bijections by construction
+            k_validate_perm<<<grid_for((uint64_t)TABLES * m), 256, 0, st>>>(d_perm, m, TABLES, d_bits.p, d_err.p);
+            BM_CHECK_LAUNCH();
+        }
         int err = 0;
         BM_CUDA(cudaMemcpyAsync(&err, d_err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
         BM_CUDA(cudaStreamSynchronize(st));
@@ -260,11 +263,11 @@ void build_witness_set(batmap_set *S, const uint64_t *d_offsets, const uint32_t 
         BM_CUDA(cudaMemsetAsync(table.p, 0xFF, S->bytes * sizeof(uint32_t), st));
         const uint32_t max_moves = TABLES * std::max<uint32_t>(P.max_loop, 1u);
         E.record(2, st);
-        k_place<<<COPIES * nch, TPB, 0, st>>>(v, S->d_perm.p, m, S->shift, max_moves, table.p);
+        k_place<<<COPIES * nch, TPB, 0, st>>>(v, PV, S->shift, max_moves, table.p);
         BM_CHECK_LAUNCH();
         E.record(3, st);
         DevBuf<uint64_t> bs(nch + 1), d_tot(1);
-        k_finalize<<<nch, TPB, 0, st>>>(v, S->d_perm.p, m, S->shift, table.p, S->d_bm.p, bs.p);
+        k_finalize<<<nch, TPB, 0, st>>>(v, PV, S->shift, table.p, S->d_bm.p, bs.p);
         BM_CHECK_LAUNCH();
         k_scan_single_block<<<1, SCAN_TPB, 0, st>>>(bs.p, nch, d_tot.p, 1);
         BM_CHECK_LAUNCH();
@@ -275,7 +278,7 @@ void build_witness_set(batmap_set *S, const uint64_t *d_offsets, const uint32_t 
         DevBuf<uint32_t> f_item(nfail);
         S->d_fail_tid.alloc(nfail);
         if (nfail) {
-            k_failures<<<nch, TPB, 0, st>>>(v, S->d_perm.p, m, S->shift, table.p, bs.p, f_item.p,
+            k_failures<<<nch, TPB, 0, st>>>(v, PV, S->shift, table.p, bs.p, f_item.p,
                                             S->d_fail_tid.p);
             BM_CHECK_LAUNCH();
         }
@@ -303,7 +306,7 @@ struct View {
     const uint32_t *bm;     // BatMap bytes as 32-bit words
     const uint64_t *base;   // [n+1] byte offset of item i
     const uint32_t *rlog;   // [n] log2 r_i (r_i words per BatMap)
-    const uint32_t *perm;   // [4 m]
+    PermView perm;          // pi_0 .. pi_3
     const uint64_t *f_off;  // [n+1] failed insertions (CSR, sorted tids)
     const uint32_t *f_tid;
     uint32_t m, n, shift;
@@ -344,7 +347,7 @@ __device__ __forceinline__ bool stored_in(const View &V, uint32_t item, uint32_t
     const uint8_t *b = reinterpret_cast<const uint8_t *>(V.bm) + V.base[item];
 #pragma unroll
     for (uint32_t t = 0; t < 2; t++) {
-        const uint32_t pi = __ldg(&V.perm[(uint64_t)t * V.m + x]);
+        const uint32_t pi = V.perm(t, x);
         if ((b[slot4(t, pi, r, V.shift)] & CODE_MASK) == code6(pi, V.shift)) return true;
     }
     return false;
@@ -737,7 +740,7 @@ void witness_support(batmap_set *S, uint32_t k, uint64_t nq, const uint32_t *d_i
         BM_CUDA(cudaStreamSynchronize(st));
         BM_REQUIRE(h == 0, BATMAP_ERR_ARG, "item id >= n in a query");
     }
-    const View V{reinterpret_cast<const uint32_t *>(S->d_bm.p), S->d_base.p, S->d_rlog.p, S->d_perm.p,
+    const View V{reinterpret_cast<const uint32_t *>(S->d_bm.p), S->d_base.p, S->d_rlog.p, S->perm,
                  S->d_fail_off.p, S->d_fail_tid.p, S->m, S->n, S->shift};
     const unsigned grid = (unsigned)std::min<uint64_t>((nq + 7) / 8, 152ull * 64);
     if (k == 1) k_witness<1><<<grid, 256, 0, st>>>(V, d_items, nq, d_support);
@@ -805,7 +808,7 @@ void frequent_triples(batmap_set *S, uint32_t s, const uint32_t *d_pairs, uint64
     if (n_cand) *n_cand = nc;
     E.record(1, st);
     if (nc) {
-        const View V{reinterpret_cast<const uint32_t *>(S->d_bm.p), S->d_base.p, S->d_rlog.p, S->d_perm.p,
+        const View V{reinterpret_cast<const uint32_t *>(S->d_bm.p), S->d_base.p, S->d_rlog.p, S->perm,
                      S->d_fail_off.p, S->d_fail_tid.p, S->m, S->n, S->shift};
         const uint64_t wpb = WG_TPB / 32;
         const unsigned grid = (unsigned)std::min<uint64_t>((n_units + wpb - 1) / wpb, 152ull * 64);

@@ -5,21 +5,37 @@ import numpy as np
 import datagen
 
 
-def device_inputs(inst, perm_seed):
+def device_inputs(inst, perm_seed, table=False):
+    """(offsets, tids, perm) on the device; perm is the caller-made table of
+    datagen.permutations when `table`, else None (the library computes its
+    permutations from params.perm_seed)."""
     import torch
     dev = torch.device("cuda:0")
     off = torch.from_numpy(inst.offsets.astype(np.int64)).to(dev)
     tids = torch.from_numpy(inst.tids.astype(np.int32)).to(dev)
-    perm = torch.from_numpy(datagen.permutations(inst.m, perm_seed).astype(np.int32)).to(dev)
+    perm = (torch.from_numpy(datagen.permutations(inst.m, perm_seed).astype(np.int32)).to(dev) if table
+            else None)
     return off, tids, perm
 
 
-def run_all_pairs(inst, s=None, perm_seed=0, params=None, want_full=True):
-    """Build + pair_support_all; returns (full uint32 packed or None, n_out, pairs uint32[k,3], set)."""
+def seeded_params(perm_seed, params=None):
+    """Build parameters (defaults, or a copy of `params`) with perm_seed set."""
+    import paper_1102_1003_gb300 as pkg
+    p = pkg.batmap_default_params()
+    if params is not None:
+        for k, _ in params._fields_:
+            setattr(p, k, getattr(params, k))
+    p.perm_seed = int(perm_seed)
+    return p
+
+
+def run_all_pairs(inst, s=None, perm_seed=0, params=None, want_full=True, table=False):
+    """Build + pair_support_all; returns (full uint32 packed or None, n_out, pairs uint32[k,3], set).
+    The permutations are the library's for seed perm_seed, or the caller-made table."""
     import torch
     import paper_1102_1003_gb300 as pkg
-    off, tids, perm = device_inputs(inst, perm_seed)
-    bset = pkg.batmap_build(inst.m, off, tids, perm, params=params)
+    off, tids, perm = device_inputs(inst, perm_seed, table)
+    bset = pkg.batmap_build(inst.m, off, tids, perm, params=seeded_params(perm_seed, params))
     npairs = inst.n * (inst.n - 1) // 2
     full = torch.empty(max(npairs, 1), dtype=torch.int32, device="cuda") if want_full else None
     n_out, pairs = pkg.pair_support_all(bset, inst.s if s is None else s, full=full)
@@ -28,14 +44,17 @@ def run_all_pairs(inst, s=None, perm_seed=0, params=None, want_full=True):
     return f, n_out, pairs.cpu().numpy().astype(np.uint32).reshape(-1, 3), bset
 
 
-def layout_errors(inst, bset, perm_seed, c_num=2, c_den=1):
+def layout_errors(inst, bset, perm_seed, c_num=2, c_den=1, table=False):
     """Check every item's BatMap against the definition (hash ranges from the
-    load factor c = c_num / c_den); returns a list of errors."""
+    load factor c = c_num / c_den, the permutations of seed perm_seed: the
+    oracle's restatement of the library's generator, or the caller-made
+    table); returns a list of errors."""
     import paper_1102_1003_gb300 as pkg
     from oracle import batmap_rules as R
+    from oracle import permutation as OP
     lay = pkg.batmap_export_layout(bset)
     info = lay["info"]
-    perms = datagen.permutations(inst.m, perm_seed)
+    perms = datagen.permutations(inst.m, perm_seed) if table else OP.permutations(inst.m, perm_seed, 3)
     s = info["shift"]
     r0 = info["r0"]
     errs = []

@@ -1,6 +1,6 @@
 """The bench's reference arm (the CPU oracle timed on the default workload)
 prints one JSON line with the keys the measurement contract needs (CPU only;
-about ten seconds)."""
+about half a minute: the 1.7e9 tids are generated in parallel)."""
 import json
 import os
 import subprocess
@@ -22,7 +22,7 @@ def test_reference_arm_line():
     assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
-    assert d["config"]["workload"] == "zipf_m1m_n2000"
+    assert d["config"]["workload"] == "bern_m4m_n8192_p5"
 
 
 def test_merge_micro_small():

@@ -48,10 +48,14 @@ def test_bernoulli_m10k_all_pairs_exact():
     assert np.array_equal(pairs, oracle.pairs_threshold(inst.offsets, inst.tids, inst.s))
 
 
-def test_bernoulli_m10k_layout_valid():
+@pytest.mark.parametrize("table", [False, True])
+def test_bernoulli_m10k_layout_valid(table):
+    """Every BatMap valid by the definition, with the library's computed
+    permutations (checked against the oracle's restatement of the generator)
+    and with a caller-made permutation table."""
     inst = datagen.workload_instance("bern_m10k_n200")
-    _, _, _, bset = run_all_pairs(inst, perm_seed=1, want_full=False)
-    assert layout_errors(inst, bset, 1) == []
+    _, _, _, bset = run_all_pairs(inst, perm_seed=1, want_full=False, table=table)
+    assert layout_errors(inst, bset, 1, table=table) == []
     info = bset.info
     assert info["n_classes"] == 2  # widths 3 KiB and 6 KiB mixed (|S| straddles 512)
 
@@ -165,11 +169,11 @@ def test_invalid_inputs_rejected():
         "out_of_range": datagen.Instance(m, 2, good.offsets, np.array([1, 5, 100, 2, 5], np.uint32)),
     }
     for name, inst in cases.items():
-        off, tids, perm = device_inputs(inst, 0)
+        off, tids, perm = device_inputs(inst, 0, table=True)
         with pytest.raises(pkg.BatmapError) as e:
             pkg.batmap_build(m, off, tids, perm)
         assert e.value.code == pkg.BATMAP_ERR_ARG, name
-    off, tids, perm = device_inputs(good, 0)
+    off, tids, perm = device_inputs(good, 0, table=True)
     bad = perm.clone()
     bad[1, 3] = bad[1, 4]
     with pytest.raises(pkg.BatmapError) as e:
@@ -187,9 +191,11 @@ def test_host_entry_point_matches_device_path():
     perm = datagen.permutations(inst.m, 5)
     ref = oracle.pairs_threshold(inst.offsets, inst.tids, inst.s)
     pinned = torch.empty((ref.shape[0] + 10) * 3, dtype=torch.int32, pin_memory=True).numpy()
-    n_out = pkg.pair_support_host(inst.m, inst.offsets, inst.tids, perm, inst.s, pinned)
-    assert n_out == ref.shape[0]
-    assert np.array_equal(pinned[:3 * n_out].reshape(-1, 3).astype(np.uint32), ref)
+    for p in (perm, None):  # a caller-made table, and the library's computed permutations
+        pinned[:] = -1
+        n_out = pkg.pair_support_host(inst.m, inst.offsets, inst.tids, p, inst.s, pinned)
+        assert n_out == ref.shape[0]
+        assert np.array_equal(pinned[:3 * n_out].reshape(-1, 3).astype(np.uint32), ref)
 
 
 def test_batch_equals_separate_calls():
@@ -226,35 +232,3 @@ def test_zipf_full_scale_exact():
     _check_exact(inst, full, n_out, pairs)
     info = bset.info
     assert info["n_classes"] >= 6
-
-
-@pytest.mark.parametrize("name", ["bern_m4m_n8192_p0.1", "bern_m4m_n8192_p1", "bern_m4m_n8192_p5"])
-def test_density_sweep_full_scale_sampled(name):
-    """The density sweep at full size (m = 4,194,304, n = 8,192, 33.5M pairs) in
-    the bench's launch configuration: 3000 sampled supports against the merge
-    oracle, whole rows through the row-sum invariant, and the frequent-pair
-    list against the supports."""
-    inst = datagen.workload_instance(name)
-    full, n_out, pairs, bset = run_all_pairs(inst, perm_seed=4)
-    n = inst.n
-    rng = np.random.default_rng(12)
-    ii = rng.integers(0, n - 1, 3000)
-    jj = ii + 1 + (rng.integers(0, n, 3000) % (n - 1 - ii))
-    ref = oracle.pairs_list(inst.offsets, inst.tids, ii, jj, threads=THREADS)
-    idx = oracle.packed_index(n, ii, jj)
-    assert np.array_equal(full[idx], ref)
-    # sum over partners of row i = sum over x in S_i of (|T_x| - 1)
-    tlen = np.bincount(inst.tids, minlength=inst.m).astype(np.int64)
-    for i in rng.integers(0, n, 12):
-        i = int(i)
-        cols = np.arange(n)
-        lo, hi = np.minimum(i, cols), np.maximum(i, cols)
-        keep = cols != i
-        row = full[oracle.packed_index(n, lo[keep], hi[keep])].astype(np.int64).sum()
-        assert row == (tlen[inst.tidlist(i)] - 1).sum()
-    # the frequent pairs are exactly the supports >= s, lexicographic
-    assert n_out == int((full >= inst.s).sum())
-    if n_out:
-        key = pairs[:, 0].astype(np.int64) * n + pairs[:, 1]
-        assert (np.diff(key) > 0).all() and (pairs[:, 0] < pairs[:, 1]).all()
-        assert np.array_equal(full[oracle.packed_index(n, pairs[:, 0], pairs[:, 1])], pairs[:, 2])

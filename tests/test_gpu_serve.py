@@ -38,17 +38,18 @@ def _queries(n, count, seed, big=None):
     return qs
 
 
-def _make_pool(inst, seed=1, params=None):
+def _make_pool(inst, seed=1, params=None, table=False):
     import paper_1102_1003_gb300 as pkg
-    off, tids, perm = device_inputs(inst, seed)
+    off, tids, perm = device_inputs(inst, seed, table)
     return pkg.batmap_pool_create(inst.m, off, tids, perm, params=params)
 
 
-@pytest.mark.parametrize("params", [None, dict(load_num=1, load_den=2, max_loop=1)])
-def test_intersect_query_exact(params):
+@pytest.mark.parametrize("params,table", [(None, False), (None, True),
+                                          (dict(load_num=1, load_den=2, max_loop=1), False)])
+def test_intersect_query_exact(params, table):
     import paper_1102_1003_gb300 as pkg
     inst = _pool_inst()
-    pool = _make_pool(inst, params=pkg.batmap_default_params(**params) if params else None)
+    pool = _make_pool(inst, params=pkg.batmap_default_params(**params) if params else None, table=table)
     info = pool.info
     assert 0 < info["n_batmaps"] < inst.n
     big = np.flatnonzero(inst.sizes >= 8192)

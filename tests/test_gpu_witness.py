@@ -24,28 +24,32 @@ def _cuda():
     torch.cuda.set_device(0)
 
 
-def _dev(inst, seed):
+def _dev(inst, seed, table=False):
+    """Device tidlists and, with `table`, a caller-made table of the four
+    permutations (else None: the library computes them from perm_seed)."""
     import torch
     off = torch.from_numpy(inst.offsets.view(np.int64)).cuda()
     tids = torch.from_numpy(inst.tids.view(np.int32)).cuda()
-    perm = torch.from_numpy(datagen.permutations(inst.m, seed, count=4).view(np.int32)).cuda()
+    perm = (torch.from_numpy(datagen.permutations(inst.m, seed, count=4).view(np.int32)).cuda() if table
+            else None)
     return off, tids, perm
 
 
-def _build(inst, seed=1, **params):
+def _build(inst, seed=1, table=False, **params):
     import paper_1102_1003_gb300 as pkg
-    off, tids, perm = _dev(inst, seed)
-    p = pkg.batmap_default_params(**params) if params else None
+    off, tids, perm = _dev(inst, seed, table)
+    p = pkg.batmap_default_params(perm_seed=seed, **params)
     return pkg.batmap_build_d(3, inst.m, off, tids, perm, params=p)
 
 
-def _layout_errors(inst, bset, seed, c_num=2, c_den=1):
+def _layout_errors(inst, bset, seed, c_num=2, c_den=1, table=False):
     import paper_1102_1003_gb300 as pkg
+    from oracle import permutation as OP
     lay = pkg.batmap_export_layout(bset)
     info = lay["info"]
     s, r0 = info["shift"], info["r0"]
     assert s == R.shift_bits(inst.m)
-    perms = datagen.permutations(inst.m, seed, count=4)
+    perms = datagen.permutations(inst.m, seed, count=4) if table else OP.permutations(inst.m, seed, 4)
     errs = []
     for i in range(inst.n):
         r = int(lay["range"][i])
@@ -62,14 +66,15 @@ def _queries(rng, n, k, q):
     return rng.integers(0, n, size=(q, k)).astype(np.int32)
 
 
-@pytest.mark.parametrize("params", [None, dict(load_num=1, load_den=1, max_loop=1)])
-def test_layout_and_kway_supports_exact(params):
+@pytest.mark.parametrize("params,table", [(None, False), (None, True),
+                                          (dict(load_num=1, load_den=1, max_loop=1), False)])
+def test_layout_and_kway_supports_exact(params, table):
     import torch
     import paper_1102_1003_gb300 as pkg
     inst = datagen.zipf_tidlists(60_000, 80, 0.04, seed=11)
-    b = _build(inst, 1, **(params or {}))
+    b = _build(inst, 1, table, **(params or {}))
     lf = (params["load_num"], params["load_den"]) if params else (2, 1)
-    errs, info = _layout_errors(inst, b, 1, *lf)
+    errs, info = _layout_errors(inst, b, 1, *lf, table=table)
     assert errs == []
     assert info["d"] == 3
     if params:
@@ -113,7 +118,7 @@ def test_edge_cases_and_rejections():
         pkg.itemset_support(b, torch.tensor([[0, 1, 6]], dtype=torch.int32, device="cuda"))
     with pytest.raises(pkg.BatmapError):
         pkg.pair_support_all(b, 1)
-    off, tids, perm = _dev(inst, 3)
+    off, tids, perm = _dev(inst, 3, table=True)
     with pytest.raises(pkg.BatmapError):
         pkg.batmap_build_d(4, inst.m, off, tids, torch.zeros(5 * inst.m, dtype=torch.int32, device="cuda"))
     # a 2-of-3 set does not answer k-way witness queries
@@ -138,11 +143,13 @@ def test_frequent_triples_exact(name, s):
             "dense": lambda: datagen.bernoulli_tidlists(2_000, 60, 0.3, seed=6),
             "zipf": lambda: datagen.zipf_tidlists(50_000, 300, 0.03, seed=5)}[name]()
     pairs_ref, cand, want = _oracle_triples(inst, s)
-    off, tids, perm4 = _dev(inst, 4)
-    b2 = pkg.batmap_build(inst.m, off, tids, perm4[:3].contiguous())
+    table = name == "dense"  # one case with caller-made permutations, the rest computed
+    off, tids, perm4 = _dev(inst, 4, table)
+    p = pkg.batmap_default_params(perm_seed=4)
+    b2 = pkg.batmap_build(inst.m, off, tids, perm4[:3].contiguous() if table else None, params=p)
     n_pairs, pairs = pkg.pair_support_all(b2, s)
     assert np.array_equal(pairs.cpu().numpy().astype(np.uint32), pairs_ref)
-    b3 = pkg.batmap_build_d(3, inst.m, off, tids, perm4)
+    b3 = pkg.batmap_build_d(3, inst.m, off, tids, perm4, params=p)
     n_out, trip, n_cand = pkg.frequent_triples(b3, s, pairs)
     assert n_cand == cand.shape[0]
     assert n_out == want.shape[0]
