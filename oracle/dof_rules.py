@@ -15,9 +15,10 @@ here (each also listed in the design notes of the repository):
     (d+1) r_0, slot h_t(x) = (d+1) r_0 floor((pi_t(x) mod r) / r_0)
     + (pi_t(x) mod r_0) + t r_0, width (d+1) r bytes, r chosen as for d = 2;
   * an 8-bit slot holds the MISSING table of the element (the one table
-    without a copy) in its top two bits and the code (pi_t(x) >> s) + 1 in
-    the low six bits (d <= 3), 0x00 = empty, so s is the smallest shift with
-    m <= 63 * 2^s;
+    without a copy) in its top bits and the code (pi_t(x) >> s) + 1 in the
+    low bits, 0x00 = empty: two missing-table bits and six code bits for
+    d = 3 (s the smallest shift with m <= 63 * 2^s), three and five for
+    d = 4 (m <= 31 * 2^s);
   * witness rule: for an intersection of k <= d sets, the copies in table t
     count iff the codes agree, the slot is not empty, and t is the SMALLEST
     table not missed by any of the k sets -- a function of t and the k
@@ -35,17 +36,30 @@ import itertools
 import numpy as np
 
 EMPTY = -1
-D = 3              # the format below is defined for d + 1 <= 4 tables
-CODE_BITS = 6
+D = 3              # the default: 3-of-4 BatMaps
+CODE_BITS = 6      # code bits of the d = 3 format
 CODE_MAX = (1 << CODE_BITS) - 1   # 63
+
+
+def missing_bits(d: int) -> int:
+    """Bits of the missing-table field: tables 0..d (2 for d = 3, 3 for d = 4)."""
+    return max(2, int(d).bit_length())
+
+
+def code_bits(d: int) -> int:
+    return 8 - missing_bits(d)
+
+
+def code_max(d: int) -> int:
+    return (1 << code_bits(d)) - 1
 
 
 # ---- sizing ----------------------------------------------------------------
 
-def shift_bits(m: int, min_shift: int = 7) -> int:
-    """Smallest s >= min_shift with m <= 63 * 2^s (6-bit codes 1..63, 0 = empty)."""
+def shift_bits(m: int, min_shift: int = 7, d: int = D) -> int:
+    """Smallest s >= min_shift with m <= code_max(d) * 2^s (codes 1..code_max, 0 = empty)."""
     s = min_shift
-    while m > CODE_MAX * (1 << s):
+    while m > code_max(d) * (1 << s):
         s += 1
     return s
 
@@ -76,8 +90,8 @@ def code6(pi, s: int):
     return (np.asarray(pi, dtype=np.int64) >> s) + 1
 
 
-def element_byte(missing: int, pi: int, s: int) -> int:
-    return (int(missing) << CODE_BITS) | int(code6(pi, s))
+def element_byte(missing: int, pi: int, s: int, d: int = D) -> int:
+    return (int(missing) << code_bits(d)) | int(code6(pi, s))
 
 
 # ---- the witness rule -----------------------------------------------------
@@ -88,12 +102,13 @@ def witness_table(missing, d: int = D):
     return free[0] if free else None
 
 
-def slot_counts(t: int, bytes_k) -> bool:
+def slot_counts(t: int, bytes_k, d: int = D) -> bool:
     """Does table t's slot holding bytes b_1..b_k count one common element?"""
-    codes = [int(b) & CODE_MAX for b in bytes_k]
+    cm, cb = code_max(d), code_bits(d)
+    codes = [int(b) & cm for b in bytes_k]
     if codes[0] == 0 or any(c != codes[0] for c in codes):
         return False
-    return witness_table([int(b) >> CODE_BITS for b in bytes_k]) == t
+    return witness_table([int(b) >> cb for b in bytes_k], d) == t
 
 
 def kway_count(bms, r0: int, d: int = D) -> int:
@@ -105,11 +120,11 @@ def kway_count(bms, r0: int, d: int = D) -> int:
     cols = [np.tile(b, W // b.size) for b in bms]
     tab = table_of_slot(np.arange(W), r0, d)
     stacked = np.stack([c.astype(np.int64) for c in cols])
-    codes = stacked & CODE_MAX
+    codes = stacked & code_max(d)
     equal = (codes == codes[0]).all(axis=0) & (codes[0] != 0)
     total = 0
     for w in np.flatnonzero(equal):
-        if witness_table(stacked[:, w] >> CODE_BITS, d) == tab[w]:
+        if witness_table(stacked[:, w] >> code_bits(d), d) == tab[w]:
             total += 1
     return total
 
@@ -172,7 +187,7 @@ def serial_layout(tids, perms, r: int, r0: int, s: int, d: int = D, max_loop: in
             missing = [u for u in range(d + 1) if bm.A[u][bm.h(u, x)] != x]
             assert len(missing) == 1
             pi = int(perms[t][x])
-            out[int(slot(t, pi, r, r0, d))] = element_byte(missing[0], pi, s)
+            out[int(slot(t, pi, r, r0, d))] = element_byte(missing[0], pi, s, d)
     return out, np.array(sorted(failed), dtype=np.uint32)
 
 
@@ -195,7 +210,7 @@ def check_layout(bm, tids, failed, perms, r: int, r0: int, s: int, d: int = D) -
     for t in range(d + 1):
         pi = perms[t][tids].astype(np.int64)
         pos[t] = slot(t, pi, r, r0, d)
-        stored[t] = (bm[pos[t]].astype(np.int64) & CODE_MAX) == code6(pi, s)
+        stored[t] = (bm[pos[t]].astype(np.int64) & code_max(d)) == code6(pi, s)
     ncopies = stored.sum(axis=0)
     if (ncopies[is_ok] != d).any():
         errs.append(f"{int((ncopies[is_ok] != d).sum())} elements without exactly {d} copies")
@@ -204,7 +219,7 @@ def check_layout(bm, tids, failed, perms, r: int, r0: int, s: int, d: int = D) -
     missing = np.argmin(stored, axis=0)
     for t in range(d + 1):
         sel = stored[t] & is_ok
-        if ((bm[pos[t][sel]] >> CODE_BITS) != missing[sel]).any():
+        if ((bm[pos[t][sel]] >> code_bits(d)) != missing[sel]).any():
             errs.append(f"missing-table field wrong in table {t}")
     nonzero = int(np.count_nonzero(bm))
     if nonzero != d * int(is_ok.sum()):
@@ -247,3 +262,28 @@ def triple_candidates_bruteforce(n: int, frequent_pairs) -> np.ndarray:
     out = [(a, b, c) for a, b, c in itertools.combinations(range(n), 3)
            if (a, b) in pairs and (a, c) in pairs and (b, c) in pairs]
     return np.array(out, dtype=np.uint32).reshape(-1, 3)
+
+
+# ---- Apriori level 4 --------------------------------------------------------
+
+def quadruple_candidates(frequent_triples) -> np.ndarray:
+    """Every a < b < c < d whose four 3-subsets are all frequent, lexicographic
+    (the Apriori join of triples sharing (a, b), pruned by the other subsets)."""
+    trip = {tuple(int(v) for v in t) for t in frequent_triples}
+    by_prefix = {}
+    for a, b, c in sorted(trip):
+        by_prefix.setdefault((a, b), []).append(c)
+    out = []
+    for (a, b), cs in sorted(by_prefix.items()):
+        for x, c in enumerate(cs):
+            for dd in cs[x + 1:]:
+                if (a, c, dd) in trip and (b, c, dd) in trip:
+                    out.append((a, b, c, dd))
+    return np.array(out, dtype=np.uint32).reshape(-1, 4)
+
+
+def quadruple_candidates_bruteforce(n: int, frequent_triples) -> np.ndarray:
+    trip = {tuple(int(v) for v in t) for t in frequent_triples}
+    out = [q for q in itertools.combinations(range(n), 4)
+           if all(tuple(x for x in q if x != y) in trip for y in q)]
+    return np.array(out, dtype=np.uint32).reshape(-1, 4)

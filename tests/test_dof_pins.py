@@ -1,8 +1,9 @@
 """Pins of the d-of-(d+1) BatMap rules (Sec. V generalisation) against things
-other than themselves (CPU only): the pigeonhole witness property checked
+other than themselves (CPU only), for d = 3 (3-of-4) and d = 4 (4-of-5, a
+three-bit missing-table field): the pigeonhole witness property checked
 exhaustively, the serial layout's counts against Python set intersections and
 the merge oracle, layout validity, planted mistakes, and the Apriori
-candidate step against brute force."""
+candidate steps (levels 3 and 4) against brute force."""
 import itertools
 
 import numpy as np
@@ -39,6 +40,19 @@ def test_slot_rule_needs_equal_nonempty_codes():
     assert [R.slot_counts(t, bs) for t in range(4)] == [False, False, False, True]
 
 
+def test_slot_rule_five_tables():
+    # d = 4: three missing-table bits, five code bits
+    assert R.missing_bits(4) == 3 and R.code_bits(4) == 5 and R.code_max(4) == 31
+    assert R.missing_bits(3) == 2 and R.code_bits(3) == 6
+    b = R.element_byte(4, 5 << 7, 7, d=4)        # missing table 4, code 6
+    assert b == (4 << 5) | 6
+    assert R.slot_counts(0, [b] * 4, d=4) and not R.slot_counts(1, [b] * 4, d=4)
+    # four sets missing tables 0..3 leave only table 4
+    bs = [R.element_byte(u, 9 << 7, 7, d=4) for u in (0, 1, 2, 3)]
+    assert [R.slot_counts(t, bs, d=4) for t in range(5)] == [False] * 4 + [True]
+    assert R.shift_bits(31 * 128, d=4) == 7 and R.shift_bits(31 * 128 + 1, d=4) == 8
+
+
 def test_sizing_boundaries():
     assert R.shift_bits(63 * 128) == 7 and R.shift_bits(63 * 128 + 1) == 8
     assert R.shift_bits(1) == 7 and R.shift_bits(10**6) == 14   # 63 * 2^14 = 1,032,192
@@ -54,47 +68,49 @@ def _instance(rng, m, n, pmax=0.4):
     return datagen.from_lists(lists, m)
 
 
-def _layouts(inst, perms, c=2, max_loop=32):
-    s = R.shift_bits(inst.m)
+def _layouts(inst, perms, c=2, max_loop=32, d=3):
+    s = R.shift_bits(inst.m, d=d)
     r0 = 1 << s
     out = []
     for i in range(inst.n):
         r = R.hash_range(inst.tidlist(i).size, r0, c, 1)
-        bm, f = R.serial_layout(inst.tidlist(i), perms, r, r0, s, 3, max_loop)
-        assert R.check_layout(bm, inst.tidlist(i), f, perms, r, r0, s) == []
+        bm, f = R.serial_layout(inst.tidlist(i), perms, r, r0, s, d, max_loop)
+        assert R.check_layout(bm, inst.tidlist(i), f, perms, r, r0, s, d) == []
         out.append((bm, f))
     return out, r0
 
 
+@pytest.mark.parametrize("d", [3, 4])
 @pytest.mark.parametrize("seed", range(6))
-def test_serial_layout_counts_match_set_intersections(seed):
+def test_serial_layout_counts_match_set_intersections(seed, d):
     rng = np.random.default_rng(seed)
     inst = _instance(rng, int(rng.integers(200, 3000)), 6)
-    perms = datagen.permutations(inst.m, seed, count=4)
-    lay, r0 = _layouts(inst, perms)
+    perms = datagen.permutations(inst.m, seed, count=d + 1)
+    lay, r0 = _layouts(inst, perms, d=d)
     sets = [set(inst.tidlist(i).tolist()) for i in range(inst.n)]
-    for k in (1, 2, 3):
+    for k in range(1, d + 1):
         for q in itertools.combinations(range(inst.n), k):
             exact = len(set.intersection(*[sets[i] for i in q]))
-            got = R.kway_count([lay[i][0] for i in q], r0) + \
+            got = R.kway_count([lay[i][0] for i in q], r0, d) + \
                 R.correction([inst.tidlist(i) for i in q], [lay[i][1] for i in q])
             assert got == exact
     # and the merge oracle agrees on the same queries
-    qs = [list(q) for q in itertools.combinations(range(inst.n), 3)]
+    qs = [list(q) for q in itertools.combinations(range(inst.n), d)]
     ref = oracle.kway_counts(inst.offsets, inst.tids, qs)
     for q, v in zip(qs, ref):
         assert v == len(set.intersection(*[sets[i] for i in q]))
 
 
-def test_forced_failures_are_corrected():
+@pytest.mark.parametrize("d", [3, 4])
+def test_forced_failures_are_corrected(d):
     rng = np.random.default_rng(7)
     inst = _instance(rng, 2000, 5, pmax=0.6)
-    perms = datagen.permutations(inst.m, 3, count=4)
-    lay, r0 = _layouts(inst, perms, c=1, max_loop=1)     # load 3/4 per table, one round
+    perms = datagen.permutations(inst.m, 3, count=d + 1)
+    lay, r0 = _layouts(inst, perms, c=1, max_loop=1, d=d)     # load d/(d+1) per table, one round
     assert sum(f.size for _, f in lay) > 0
     sets = [set(inst.tidlist(i).tolist()) for i in range(inst.n)]
-    for q in itertools.combinations(range(inst.n), 3):
-        got = R.kway_count([lay[i][0] for i in q], r0) + \
+    for q in itertools.combinations(range(inst.n), d):
+        got = R.kway_count([lay[i][0] for i in q], r0, d) + \
             R.correction([inst.tidlist(i) for i in q], [lay[i][1] for i in q])
         assert got == len(set.intersection(*[sets[i] for i in q]))
 
@@ -147,3 +163,59 @@ def test_frequent_triples_by_brute_force():
     want = {q for q in itertools.combinations(range(inst.n), 3)
             if len(set.intersection(*[sets[i] for i in q])) >= s}
     assert got == want
+
+
+def test_planted_mistakes_are_caught_five_tables():
+    rng = np.random.default_rng(4)
+    inst = _instance(rng, 3000, 5, pmax=0.7)
+    perms = datagen.permutations(inst.m, 2, count=5)
+    lay, r0 = _layouts(inst, perms, d=4)
+    sets = [set(inst.tidlist(i).tolist()) for i in range(inst.n)]
+    q = (0, 1, 2, 3)
+    exact = len(set.intersection(*[sets[i] for i in q]))
+    corr = R.correction([inst.tidlist(i) for i in q], [lay[i][1] for i in q])
+    assert R.kway_count([lay[i][0] for i in q], r0, 4) + corr == exact
+    cm, cb = R.code_max(4), R.code_bits(4)
+    # one set claiming to miss table 0 everywhere moves witnesses off their tables
+    bad = lay[2][0].copy()
+    nz = np.flatnonzero(bad)
+    bad[nz] = bad[nz] & cm
+    assert R.kway_count([lay[0][0], lay[1][0], bad, lay[3][0]], r0, 4) + corr != exact
+    # reading a five-table layout with the four-table fields (d = 3) miscounts
+    assert R.kway_count([lay[i][0] for i in q], r0, 3) + corr != exact
+    W = max(lay[i][0].size for i in q)
+    cols = [np.tile(lay[i][0], W // lay[i][0].size) & cm for i in q]
+    every = int(((cols[0] == cols[1]) & (cols[1] == cols[2]) & (cols[2] == cols[3]) & (cols[0] != 0)).sum())
+    assert exact > 0 and every + corr > exact
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_quadruple_candidates_match_bruteforce(seed):
+    rng = np.random.default_rng(seed)
+    n = 11
+    allt = list(itertools.combinations(range(n), 3))
+    keep = [t for t in allt if rng.random() < 0.6]
+    a = R.quadruple_candidates(keep)
+    b = R.quadruple_candidates_bruteforce(n, keep)
+    assert np.array_equal(a, b)
+    if a.shape[0] > 1:
+        key = ((a[:, 0].astype(np.int64) * n + a[:, 1]) * n + a[:, 2]) * n + a[:, 3]
+        assert (np.diff(key) > 0).all()
+
+
+def test_frequent_quadruples_by_brute_force():
+    # Apriori level 4 on a tiny instance equals scanning every 4-subset
+    rng = np.random.default_rng(6)
+    inst = _instance(rng, 300, 9, pmax=0.7)
+    s = 20
+    sets = [set(inst.tidlist(i).tolist()) for i in range(inst.n)]
+    pairs = oracle.pairs_threshold(inst.offsets, inst.tids, s)[:, :2]
+    cand3 = R.triple_candidates(pairs)
+    sup3 = oracle.kway_counts(inst.offsets, inst.tids, cand3.tolist())
+    trip = cand3[sup3 >= s]
+    cand4 = R.quadruple_candidates(trip)
+    sup4 = oracle.kway_counts(inst.offsets, inst.tids, cand4.tolist())
+    got = {tuple(c) for c, v in zip(cand4.tolist(), sup4) if v >= s}
+    want = {q for q in itertools.combinations(range(inst.n), 4)
+            if len(set.intersection(*[sets[i] for i in q])) >= s}
+    assert got == want and len(want) > 0
