@@ -107,25 +107,27 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def _traffic_record(workload: str, record: str = "compare_traffic.json", source: str = "compare.cu"):
-    """DRAM bytes per launch of a kernel from a committed ncu record, or None if
-    the record is for another workload or the kernel's source file changed
-    since it was taken."""
-    path = os.path.join(ROOT, "profiles", record)
-    try:
-        rec = json.load(open(path))
-    except (OSError, ValueError):
-        return None
+def _traffic_record(workload: str, kernel: str = "k_compare", source: str = "compare.cu"):
+    """DRAM bytes per launch of a kernel from a committed ncu record
+    (profiles/*traffic*.json: kernel, workload, SHA-256 of the kernel's source
+    file), or None if no record matches this workload or the source changed
+    since the counters were taken."""
+    import glob
     src = open(os.path.join(ROOT, "paper_1102_1003_gb300", "csrc", source), "rb").read()
-    if rec.get(source.replace(".", "_") + "_sha256") != hashlib.sha256(src).hexdigest():
-        return None
-    if rec.get("workload") != workload:
-        return None
-    return rec
+    digest = hashlib.sha256(src).hexdigest()
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*traffic*.json"))):
+        try:
+            rec = json.load(open(path))
+        except (OSError, ValueError):
+            continue
+        if (rec.get("kernel") == kernel and rec.get("workload") == workload
+                and rec.get(source.replace(".", "_") + "_sha256") == digest):
+            return rec
+    return None
 
 
-def _traffic(workload: str, record: str = "compare_traffic.json", source: str = "compare.cu"):
-    rec = _traffic_record(workload, record, source)
+def _traffic(workload: str, kernel: str = "k_compare", source: str = "compare.cu"):
+    rec = _traffic_record(workload, kernel, source)
     return rec["traffic_bytes_per_launch"] if rec else None
 
 
@@ -256,12 +258,17 @@ def dense_leg(args, inst, off, tids, n_out_ref, peaks, peak_kind, steps=None, wa
             "phases_ms": {"bitmap": statistics.mean(build), "tensor_kernel": statistics.mean(gemm)},
             "roofline": {"bound": "tensor", "achieved": flops_alg / g / 1e12, "peak": peak, "unit": "TFLOP/s",
                          "frac": flops_alg / g / 1e12 / peak, "kernel": "k_dense_mmt",
-                         "traffic": _traffic(workload or args.workload, "dense_traffic.json", "dense.cu"),
+                         "traffic": _traffic(workload or args.workload, "k_dense_mmt", "dense.cu"),
                          "peak_kind": f"e4m3 dense = 2 x {peak_kind} bf16 burst (nominal 4.5/2.25 ratio)",
                          "algorithmic_flops": "2 m n(n-1)/2 (pairs i < j only)",
                          "issued_TFLOPs": flops_issued / g / 1e12,
                          "issued_frac": flops_issued / g / 1e12 / peak},
             "dtype": "e4m3 {0,1} operands, fp32 accumulate (exact integers < 2^24)"}
+
+
+def _desc(workload: str) -> str:
+    base, _, first = workload.partition("_first")
+    return WORKLOAD_DESC[base] + (f", first {first} items only (profiling case)" if first else "")
 
 
 def _alu_peak(dev, peaks):
@@ -328,7 +335,7 @@ def plain_leg(inst, dev, steps, warmup, peaks, peak_kind, workload, sampler=None
     rec = {
         "value": npairs * steps / elapsed, "unit": UNIT, "steps": steps, "warmup": warmup,
         "ms_per_step": 1e3 * elapsed / steps, "elapsed_s": elapsed,
-        "config": {"workload": workload, "desc": WORKLOAD_DESC[workload], "m": inst.m, "n": inst.n,
+        "config": {"workload": workload, "desc": _desc(workload), "m": inst.m, "n": inst.n,
                    "s": inst.s, "pairs": npairs, "tids": int(inst.tids.size), "batmap_bytes": info["bytes"],
                    "width_classes": info["n_classes"], "l2": "inputs larger than L2 (no flush)"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
@@ -363,7 +370,8 @@ def run_mine(args, inst, rank, world):
     pkg.load_library()
     peaks, peak_kind = _peaks()
     npairs = inst.n * (inst.n - 1) // 2
-    rec, off, tids, n_out = plain_leg(inst, dev, args.steps, args.warmup, peaks, peak_kind, args.workload,
+    label = args.workload if not args.scale_n else f"{args.workload}_first{args.scale_n}"
+    rec, off, tids, n_out = plain_leg(inst, dev, args.steps, args.warmup, peaks, peak_kind, label,
                                       sampler=ClockSampler(local), dist=dist)
 
     # end to end through the C ABI from pinned host buffers (library-made permutations)
@@ -401,7 +409,7 @@ def run_mine(args, inst, rank, world):
         "clocks": rec["clocks"],
     }
     if not args.no_dense and inst.m <= (1 << 24):
-        line["dense"] = dense_leg(args, inst, off, tids, n_out, peaks, peak_kind)
+        line["dense"] = dense_leg(args, inst, off, tids, n_out, peaks, peak_kind, workload=label)
     del off, tids
     pkg.batmap_release_scratch()
     torch.cuda.empty_cache()
@@ -411,7 +419,7 @@ def run_mine(args, inst, rank, world):
                                 "sample": f"{k} uniformly sampled pairs of the same workload, {dt:.1f} s "
                                           "(single-threaded sorted merge on disjoint blocks, one per core)",
                                 "merge_micro": merge_micro()}
-    if world == 1 and not args.no_sub:
+    if world == 1 and not args.no_sub and not args.scale_n:
         sub = {}
         if args.workload != "zipf_m1m_n2000":
             z = datagen.workload_instance("zipf_m1m_n2000")
@@ -776,7 +784,7 @@ def run_triples(args):
                           "candidates_compact": statistics.mean(r[4]["compact_ms"] for r in rec)},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
                          "frac": achieved / alu_peak, "kernel": "k_witness_group",
-                         "traffic": _traffic("triples", "witness_traffic.json", "witness.cu"),
+                         "traffic": _traffic("triples", "k_witness_group", "witness.cu"),
                          "peak_kind": f"{sms} SMs x 128 INT32 lanes x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz "
                                       f"({peak_kind} max clock)",
                          "algorithmic_ops": f"{WITNESS_OPS} x {wt:.4g} word-triples (max_j r_j words per candidate)",
@@ -892,6 +900,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-dense", action="store_true", help="skip the dense tensor-core comparison leg")
+    ap.add_argument("--scale-n", type=int, default=None,
+                    help="keep only the first N items of the workload (small profiling cases)")
     ap.add_argument("--no-sub", action="store_true",
                     help="skip the sub-records (Zipf workload, batched vs plain) of the default line")
     args = ap.parse_args()
@@ -902,7 +912,7 @@ def main():
             {"serve": run_serve, "batch": run_batch, "nsweep": run_nsweep, "cross": run_cross,
              "triples": run_triples}[args.workload](args)
         return
-    inst = datagen.workload_instance(args.workload, workers=os.cpu_count() or 8)
+    inst = datagen.workload_instance(args.workload, scale_n=args.scale_n, workers=os.cpu_count() or 8)
     if args.impl == "reference":
         run_reference(args, inst, rank, world)
     else:

@@ -333,8 +333,9 @@ typedef struct batmap_out {
  * Returns BATMAP_ERR_CAPACITY if any instance overflowed its buffer (that
  * instance's first cap triples are written).  Synchronises the stream.
  * Afterwards batmap_get_timing of every set of the batch reports the batched
- * pass: compare_ms = the one compare launch over all instances, compact_ms =
- * all corrections and compactions, pairs_ms = the whole pass.
+ * pass: compare_ms = the one compare launch over all instances (the span of
+ * its CTAs on the GPU's global timer), pairs_ms = the whole pass (events
+ * around it), compact_ms = the rest (zeroing, corrections, compactions).
  */
 batmap_status pair_support_batch(batmap_set *const *sets, const uint32_t *s, uint32_t k,
                                  batmap_out *outs, cudaStream_t stream);

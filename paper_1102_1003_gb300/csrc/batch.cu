@@ -30,7 +30,8 @@ struct BatchPlan {
     cudaStream_t stream = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    PhaseEvents ev;  // recorded by the graph: 0 start, 1 / 2 around the compare, 3 end
+    DevBuf<unsigned long long> d_stamps;  // the compare's span: earliest CTA start, latest CTA end (ns)
+    PhaseEvents ev;                       // 0 / 1 around the graph launch (on the stream, not captured)
     ~BatchPlan() {
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
@@ -57,18 +58,16 @@ static std::vector<uint64_t> plan_key(batmap_set *const *sets, const uint32_t *s
 
 static void enqueue_batch(BatchPlan *P, batmap_set *const *sets, const uint32_t *s, uint32_t k,
                           const batmap_out *outs, cudaStream_t st) {
-    P->ev.record(0, st);
     for (uint32_t q = 0; q < k; q++) {
         const uint64_t np = sets[q]->npairs();
         if (np) BM_CUDA(cudaMemsetAsync(P->C[q], 0, np * sizeof(uint32_t), st));
     }
     BM_CUDA(cudaMemsetAsync(P->d_counter.p, 0, 2 * sizeof(uint32_t), st));
-    P->ev.record(1, st);
-    launch_compare(P->d_views.p, P->d_units.p, P->nunits, P->nmain, P->d_counter.p, st);
-    P->ev.record(2, st);
+    BM_CUDA(cudaMemsetAsync(P->d_stamps.p, 0xFF, sizeof(unsigned long long), st));
+    BM_CUDA(cudaMemsetAsync(P->d_stamps.p + 1, 0, sizeof(unsigned long long), st));
+    launch_compare(P->d_views.p, P->d_units.p, P->nunits, P->nmain, P->d_counter.p, st, P->d_stamps.p);
     for (uint32_t q = 0; q < k; q++)
         enqueue_correct_compact(sets[q], P->C[q], s[q], outs[q].d_pairs, outs[q].cap, P->d_totals.p + q, st);
-    P->ev.record(3, st);
 }
 
 static BatchPlan *make_plan(batmap_set *const *sets, const uint32_t *s, uint32_t k, const batmap_out *outs,
@@ -102,6 +101,7 @@ static BatchPlan *make_plan(batmap_set *const *sets, const uint32_t *s, uint32_t
     P->d_units.alloc(units.size());
     P->d_counter.alloc(2);
     P->d_totals.alloc(k);
+    P->d_stamps.alloc(2);
     BM_CUDA(cudaMemcpyAsync(P->d_views.p, views.data(), k * sizeof(InstView), cudaMemcpyHostToDevice, st));
     if (!units.empty())
         BM_CUDA(cudaMemcpyAsync(P->d_units.p, units.data(), units.size() * sizeof(WorkUnit),
@@ -151,13 +151,20 @@ void run_batch(batmap_set *const *sets, const uint32_t *s, uint32_t k, batmap_ou
         g_plan.reset(make_plan(sets, s, k, outs, st, std::move(key)));
     }
     BatchPlan *P = g_plan.get();
+    P->ev.record(0, st);
     BM_CUDA(cudaGraphLaunch(P->exec, st));
+    P->ev.record(1, st);
     std::vector<uint64_t> totals(k);
+    unsigned long long stamps[2] = {0, 0};
     BM_CUDA(cudaMemcpyAsync(totals.data(), P->d_totals.p, k * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    BM_CUDA(cudaMemcpyAsync(stamps, P->d_stamps.p, sizeof(stamps), cudaMemcpyDeviceToHost, st));
     BM_CUDA(cudaStreamSynchronize(st));
     // every set of the batch reports the batched pass: the one compare launch
-    // over all instances and the corrections + compactions after it
-    const float cmp = P->ev.ms(1, 2), cc = P->ev.ms(2, 3), all = P->ev.ms(0, 3);
+    // over all instances (its CTAs' globaltimer span) and the rest of the pass
+    // (zeroing, corrections, compactions)
+    const float all = P->ev.ms(0, 1);
+    const float cmp = stamps[1] > stamps[0] ? (float)((double)(stamps[1] - stamps[0]) * 1e-6) : 0.f;
+    const float cc = all > cmp ? all - cmp : 0.f;
     bool overflow = false;
     for (uint32_t q = 0; q < k; q++) {
         outs[q].n_out = totals[q];

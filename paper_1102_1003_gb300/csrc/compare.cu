@@ -463,13 +463,29 @@ static size_t max_smem_bytes() {
     return m;
 }
 
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Optional span stamps of a launch (nullptr: none): stamps[0] <- earliest CTA
+// start, stamps[1] <- latest CTA end, in globaltimer nanoseconds.
+__device__ __forceinline__ void stamp_start(unsigned long long *stamps) {
+    if (stamps && threadIdx.x == 0) atomicMin(&stamps[0], (unsigned long long)global_ns());
+}
+__device__ __forceinline__ void stamp_end(unsigned long long *stamps) {
+    if (stamps && threadIdx.x == 0) atomicMax(&stamps[1], (unsigned long long)global_ns());
+}
+
 // Persistent compare kernel: each CTA pulls units (longest first) from the
 // queue until it is empty.  Every unit names its tile shape and instance.
 __global__ void __launch_bounds__(256, 1)
 k_compare(const InstView *__restrict__ views, const WorkUnit *__restrict__ units, uint32_t count,
-          uint32_t *__restrict__ counter) {
+          uint32_t *__restrict__ counter, unsigned long long *stamps) {
     extern __shared__ __align__(16) uint4 smem[];
     __shared__ uint32_t s_unit;
+    stamp_start(stamps);
     for (;;) {
         if (threadIdx.x == 0) s_unit = atomicAdd(counter, 1u);
         __syncthreads();
@@ -488,6 +504,7 @@ k_compare(const InstView *__restrict__ views, const WorkUnit *__restrict__ units
             default: break;
         }
     }
+    stamp_end(stamps);
 }
 
 // The one-column-per-thread shapes run in a kernel of their own (after the
@@ -495,9 +512,10 @@ k_compare(const InstView *__restrict__ views, const WorkUnit *__restrict__ units
 // of the main shapes' loops untouched.
 __global__ void __launch_bounds__(256, 1)
 k_compare_small(const InstView *__restrict__ views, const WorkUnit *__restrict__ units, uint32_t count,
-                uint32_t *__restrict__ counter) {
+                uint32_t *__restrict__ counter, unsigned long long *stamps) {
     extern __shared__ __align__(16) uint4 smem[];
     __shared__ uint32_t s_unit;
+    stamp_start(stamps);
     for (;;) {
         if (threadIdx.x == 0) s_unit = atomicAdd(counter, 1u);
         __syncthreads();
@@ -513,6 +531,7 @@ k_compare_small(const InstView *__restrict__ views, const WorkUnit *__restrict__
             default: break;
         }
     }
+    stamp_end(stamps);
 }
 
 static size_t g_compare_smem = 0, g_small_smem = 0;
@@ -534,17 +553,18 @@ void prepare_compare() {
 bool small_shape(uint32_t shape) { return (shape & UNIT_SHAPE_MASK) >= 13; }
 
 void launch_compare(const InstView *d_views, const WorkUnit *d_units, uint32_t count, uint32_t nmain,
-                    uint32_t *d_counters, cudaStream_t st) {
+                    uint32_t *d_counters, cudaStream_t st, unsigned long long *d_stamps) {
     if (!count) return;
     prepare_compare();
     const uint32_t sms = (uint32_t)device_sms();
     if (nmain) {
-        k_compare<<<std::min(nmain, sms), 256, g_compare_smem, st>>>(d_views, d_units, nmain, d_counters);
+        k_compare<<<std::min(nmain, sms), 256, g_compare_smem, st>>>(d_views, d_units, nmain, d_counters, d_stamps);
         BM_CHECK_LAUNCH();
     }
     if (count > nmain) {
         k_compare_small<<<std::min(count - nmain, sms), 256, g_small_smem, st>>>(d_views, d_units + nmain,
-                                                                                count - nmain, d_counters + 1);
+                                                                                count - nmain, d_counters + 1,
+                                                                                d_stamps);
         BM_CHECK_LAUNCH();
     }
 }

@@ -41,9 +41,11 @@ uint32_t main_units(const std::vector<WorkUnit> &units);  // length of the first
 // Launch the persistent compare kernels over `count` units at d_units (any
 // mix of instances) ordered by sort_units, the first nmain of the main
 // shapes: one kernel per part, pulling work from d_counters[0] and
-// d_counters[1] (zeroed by the caller).  One CTA per SM.
+// d_counters[1] (zeroed by the caller).  One CTA per SM.  d_stamps (optional,
+// set by the caller to {~0, 0}) receives the earliest CTA start and latest CTA
+// end in globaltimer nanoseconds (timing inside captured graphs).
 void launch_compare(const InstView *d_views, const WorkUnit *d_units, uint32_t count, uint32_t nmain,
-                    uint32_t *d_counters, cudaStream_t st);
+                    uint32_t *d_counters, cudaStream_t st, unsigned long long *d_stamps = nullptr);
 
 // Sets the kernel's shared-memory attribute (call before stream capture).
 void prepare_compare();
