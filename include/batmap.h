@@ -74,7 +74,8 @@ typedef int batmap_status;
  *   perm_seed : seed of the permutations pi_t that the library computes when
  *       a build is given no permutation table (d_perm = NULL).  Sec. III-A
  *       draws pi_1..pi_3 at random without fixing a generator; the library's
- *       pi_t (t = 0, 1, 2, and 3 for 3-of-4 sets) is defined as follows.
+ *       pi_t (t = 0, 1, 2; up to 4 for 3-of-4 and 4-of-5 sets) is defined as
+ *       follows.
  *       Round keys: SplitMix64 (Steele, Lea, Flood 2014) started from the
  *       seed; table t takes outputs 4t .. 4t+3, low 32 bits each.  One pass
  *       E_t: a four-round balanced Feistel network on b bits, b the smallest
@@ -169,35 +170,39 @@ batmap_status batmap_build_cross(const batmap_params *p, uint32_t m, uint32_t n_
  * d-of-(d+1) BatMaps, the generalisation that closes Sec. V: every element is
  * kept in d of d+1 hashed tables, so the sets of any itemset of size up to d
  * share a table that witnesses each common element.  d = 2 is batmap_build
- * (the paper's 2-of-3 format; all pair calls apply).  d = 3 builds 3-of-4
- * BatMaps for k-way supports (itemset_support, frequent_triples only):
- *   width 4 r_i bytes (four tables interleaved in blocks of r_0), slot
- *   h_t(x) = 4 r_0 floor((pi_t(x) mod r_i)/r_0) + (pi_t(x) mod r_0) + t r_0,
- *   byte = (missing table << 6) | ((pi_t(x) >> s) + 1), 0x00 empty, s the
- *   smallest shift >= min_shift with m <= 63 * 2^s; elements left with fewer
- *   than three copies are failed insertions (F_i), corrected exactly.
+ * (the paper's 2-of-3 format; all pair calls apply).  d = 3 and d = 4 build
+ * 3-of-4 and 4-of-5 BatMaps for k-way supports (itemset_support,
+ * frequent_triples, frequent_quadruples only):
+ *   width (d+1) r_i bytes (d+1 tables interleaved in blocks of r_0), slot
+ *   h_t(x) = (d+1) r_0 floor((pi_t(x) mod r_i)/r_0) + (pi_t(x) mod r_0)
+ *   + t r_0; the byte holds the element's missing table in its top bits and
+ *   the code (pi_t(x) >> s) + 1 in the rest, 0x00 empty: d = 3: two missing
+ *   bits, six code bits, s the smallest shift >= min_shift with
+ *   m <= 63 * 2^s; d = 4: three missing bits, five code bits, m <= 31 * 2^s;
+ *   elements left with fewer than d copies are failed insertions (F_i),
+ *   corrected exactly.
  *   d_perm : device uint32[(d+1) * m], rows pi_0 .. pi_d (the library keeps a
- *            copy for d = 3), or NULL for the computed permutations of
+ *            copy for d >= 3), or NULL for the computed permutations of
  *            p->perm_seed (rows t = 0 .. d).  Other arguments as batmap_build.
  * Items keep their original order (no width sort); h_bytes of
  * batmap_export_layout follow it.  Errors: BATMAP_ERR_ARG for d outside
- * {2, 3} or invalid input.
+ * {2, 3, 4} or invalid input.
  */
 batmap_status batmap_build_d(const batmap_params *p, uint32_t d, uint32_t m, uint32_t n,
                              const uint64_t *d_offsets, const uint32_t *d_tids, const uint32_t *d_perm,
                              cudaStream_t stream, batmap_set **out);
 
 /*
- * |S_a1 ∩ ... ∩ S_ak| for n_q queries of k item ids (k = 1, 2 or 3) on a set
- * built with d = 3, by the witness rule: the slot of table t counts iff the
- * six code bits of the k bytes agree and are nonzero and t is the smallest
- * table missed by none of the k sets (read from the bytes' top two bits);
- * failed common elements are added from the F lists.
+ * |S_a1 ∩ ... ∩ S_ak| for n_q queries of k item ids (1 <= k <= d) on a set
+ * built with d = 3 or d = 4, by the witness rule: the slot of table t counts
+ * iff the code bits of the k bytes agree and are nonzero and t is the
+ * smallest table missed by none of the k sets (read from the bytes' missing-
+ * table fields); failed common elements are added from the F lists.
  *   d_items   : device uint32[k * n_q], query q = d_items[k q .. k q + k),
  *               ids < n (checked; repeats allowed).
  *   d_support : device uint32[n_q] (written).
  * Asynchronous apart from the id check (one stream synchronisation).
- * Errors: BATMAP_ERR_ARG (d != 3, k out of range, id >= n, NULL pointer).
+ * Errors: BATMAP_ERR_ARG (d not 3 or 4, k out of range, id >= n, NULL pointer).
  */
 batmap_status itemset_support(batmap_set *set, uint32_t k, uint64_t n_q, const uint32_t *d_items,
                               uint32_t *d_support, cudaStream_t stream);
@@ -213,14 +218,36 @@ batmap_status itemset_support(batmap_set *set, uint32_t k, uint64_t n_q, const u
  *   d_out   : device uint32[4 * cap], (a, b, c, support), lexicographic.
  *   n_out   : host, number of frequent triples (all of them, even > cap).
  *   n_candidates : host, may be NULL; number of candidates counted.
- * Synchronises `stream`.  Timing: compare_ms = the support kernel,
- * compact_ms = candidate generation + compaction, pairs_ms = the call.
- * Errors: BATMAP_ERR_ARG, BATMAP_ERR_CAPACITY (cap < *n_out; the first cap
- * triples are written).
+ * The set may be built with d = 3 (grouped witness kernel) or d = 4 (one
+ * warp per candidate).  Synchronises `stream`.  Timing: compare_ms = the
+ * support kernel, compact_ms = candidate generation + compaction, pairs_ms =
+ * the call.  Errors: BATMAP_ERR_ARG, BATMAP_ERR_CAPACITY (cap < *n_out; the
+ * first cap triples are written).
  */
 batmap_status frequent_triples(batmap_set *set, uint32_t s, const uint32_t *d_pairs, uint64_t n_pairs,
                                uint32_t *d_out, uint64_t cap, uint64_t *n_out, uint64_t *n_candidates,
                                cudaStream_t stream);
+
+/*
+ * Frequent itemsets of size 4 (the problem of Sec. I, Apriori level 4): the
+ * frequent triples sharing their first two items are joined into candidates
+ * {a < b < c < d}, those whose other two 3-subsets are not frequent are
+ * pruned, itemset_support counts the rest on a 4-of-5 set, and those with
+ * support >= s are written.
+ *   d_triples : device uint32[4 * n_triples], (a, b, c, support) with
+ *               a < b < c < n in lexicographic order: the output of
+ *               frequent_triples for the same tidlists and threshold s
+ *               (checked: order and ids).
+ *   d_out     : device uint32[5 * cap], (a, b, c, d, support), lexicographic.
+ *   n_out     : host, number of frequent quadruples (all of them, even > cap).
+ *   n_candidates : host, may be NULL; number of candidates counted.
+ * Needs a set built with d = 4.  Synchronises `stream`; timing as
+ * frequent_triples.  Errors: BATMAP_ERR_ARG, BATMAP_ERR_CAPACITY (the first
+ * cap quadruples are written).
+ */
+batmap_status frequent_quadruples(batmap_set *set, uint32_t s, const uint32_t *d_triples, uint64_t n_triples,
+                                  uint32_t *d_out, uint64_t cap, uint64_t *n_out, uint64_t *n_candidates,
+                                  cudaStream_t stream);
 
 /* Release a handle and all device memory it owns (NULL is ignored). */
 void batmap_free(batmap_set *set);

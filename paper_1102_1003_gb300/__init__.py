@@ -14,4 +14,5 @@ from .batmap import (  # noqa: F401
     BatMapPool, batmap_pool_create, batmap_pool_free, batmap_pool_info, intersect_query, batmap_serve,
     batmap_serve_opts, batmap_autotune, batmap_release_scratch, intersect_query_list, batmap_build_cross,
     batmap_build_d, itemset_support, frequent_triples, batmap_test_dense_timeout,
+    frequent_quadruples,
 )

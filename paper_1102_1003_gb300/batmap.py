@@ -30,6 +30,7 @@ EXPORTED = [
     "pair_support_dense", "batmap_pool_create", "batmap_pool_free", "batmap_pool_info", "intersect_query",
     "batmap_serve", "batmap_autotune", "batmap_release_scratch", "intersect_query_list", "batmap_build_cross",
     "batmap_build_d", "itemset_support", "frequent_triples", "batmap_test_dense_timeout",
+    "frequent_quadruples",
 ]
 
 
@@ -156,6 +157,8 @@ def load_library(path: str = LIB_PATH):
     L.itemset_support.restype = ctypes.c_int
     L.frequent_triples.argtypes = [vp, u32, vp, u64, vp, u64, ctypes.POINTER(u64), ctypes.POINTER(u64), vp]
     L.frequent_triples.restype = ctypes.c_int
+    L.frequent_quadruples.argtypes = [vp, u32, vp, u64, vp, u64, ctypes.POINTER(u64), ctypes.POINTER(u64), vp]
+    L.frequent_quadruples.restype = ctypes.c_int
     L.batmap_test_dense_timeout.argtypes = [u32]
     L.batmap_test_dense_timeout.restype = None
     _lib = L
@@ -292,13 +295,13 @@ def batmap_build_cross(m: int, n_a: int, offsets, tids, perm=None, params: batma
 
 def batmap_build_d(d: int, m: int, offsets, tids, perm=None, params: batmap_params | None = None,
                    stream=None) -> BatMapSet:
-    """d-of-(d+1) BatMaps (Sec. V generalisation): d = 2 is batmap_build; d = 3 builds
-    3-of-4 BatMaps for itemset_support / frequent_triples.  perm: cuda [d+1, m] or None
-    (computed from params.perm_seed)."""
+    """d-of-(d+1) BatMaps (Sec. V generalisation): d = 2 is batmap_build; d = 3 and 4 build
+    3-of-4 and 4-of-5 BatMaps for itemset_support / frequent_triples / frequent_quadruples.
+    perm: cuda [d+1, m] or None (computed from params.perm_seed)."""
     _check_inputs(offsets, tids, perm)
     L = load_library()
     n = int(offsets.numel()) - 1
-    if perm is not None and d in (2, 3) and int(m) >= 1 and int(perm.numel()) != (d + 1) * int(m):
+    if perm is not None and d in (2, 3, 4) and int(m) >= 1 and int(perm.numel()) != (d + 1) * int(m):
         raise ValueError(f"perm must hold {d + 1} rows of m = {m} entries")
     h = ctypes.c_void_p()
     pp = ctypes.byref(params) if params is not None else None
@@ -342,6 +345,29 @@ def frequent_triples(bset: BatMapSet, s: int, pairs, out=None, stream=None):
     _check(rc, allow=(BATMAP_ERR_CAPACITY,))
     k = min(int(n_out.value), cap)
     return int(n_out.value), out.view(-1, 4)[:k], int(n_cand.value)
+
+
+def frequent_quadruples(bset: BatMapSet, s: int, triples, out=None, stream=None):
+    """Frequent itemsets of size 4 from the frequent triples (cuda int32 [k, 4], the
+    output of frequent_triples with the same s) on a 4-of-5 set; returns (n_out,
+    quadruples view [min(n_out, cap), 5] of (a, b, c, d, support), n_candidates)."""
+    import torch
+    L = load_library()
+    nt = int(triples.shape[0])
+    n_out, n_cand = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    st = _stream_handle(stream)
+    tp = _ptr(triples) if nt else None
+    if out is None:
+        rc = L.frequent_quadruples(bset.handle, int(s), tp, nt, None, 0, ctypes.byref(n_out),
+                                   ctypes.byref(n_cand), st)
+        _check(rc, allow=(BATMAP_ERR_CAPACITY,))
+        out = torch.empty((max(int(n_out.value), 1), 5), dtype=torch.int32, device="cuda")
+    cap = out.numel() // 5
+    rc = L.frequent_quadruples(bset.handle, int(s), tp, nt, _ptr(out), cap, ctypes.byref(n_out),
+                               ctypes.byref(n_cand), st)
+    _check(rc, allow=(BATMAP_ERR_CAPACITY,))
+    k = min(int(n_out.value), cap)
+    return int(n_out.value), out.view(-1, 5)[:k], int(n_cand.value)
 
 
 def batmap_free(bset: BatMapSet):

@@ -22,6 +22,8 @@ void witness_support(batmap_set *S, uint32_t k, uint64_t nq, const uint32_t *d_i
                      cudaStream_t st);
 void frequent_triples(batmap_set *S, uint32_t s, const uint32_t *d_pairs, uint64_t np, uint32_t *d_out,
                       uint64_t cap, uint64_t *n_out, uint64_t *n_cand, cudaStream_t st);
+void frequent_quadruples(batmap_set *S, uint32_t s, const uint32_t *d_triples, uint64_t nt, uint32_t *d_out,
+                         uint64_t cap, uint64_t *n_out, uint64_t *n_cand, cudaStream_t st);
 void enqueue_correct_compact(batmap_set *S, uint32_t *C, uint32_t s, uint32_t *d_pairs, uint64_t cap,
                              uint64_t *d_total, cudaStream_t st);
 void run_batch(batmap_set *const *sets, const uint32_t *s, uint32_t k, batmap_out *outs, cudaStream_t st);
@@ -106,7 +108,7 @@ static batmap_status build_any(const batmap_params *p, uint32_t m, uint32_t n, u
         S->d = d;
         S->gen = g_gen.fetch_add(1);
         try {
-            if (d == 3) build_witness_set(S, d_offsets, d_tids, d_perm);
+            if (d == 3 || d == 4) build_witness_set(S, d_offsets, d_tids, d_perm);
             else build_set(S, d_offsets, d_tids, d_perm);
         } catch (...) {
             delete S;
@@ -139,8 +141,8 @@ batmap_status batmap_build_cross(const batmap_params *p, uint32_t m, uint32_t n_
 batmap_status batmap_build_d(const batmap_params *p, uint32_t d, uint32_t m, uint32_t n,
                              const uint64_t *d_offsets, const uint32_t *d_tids, const uint32_t *d_perm,
                              cudaStream_t stream, batmap_set **out) {
-    if (d != 2 && d != 3) {
-        set_error("d must be 2 or 3");
+    if (d < 2 || d > 4) {
+        set_error("d must be 2, 3 or 4");
         return BATMAP_ERR_ARG;
     }
     return build_any(p, m, n, 0, d_offsets, d_tids, d_perm, stream, out, d);
@@ -155,6 +157,13 @@ batmap_status frequent_triples(batmap_set *S, uint32_t s, const uint32_t *d_pair
                                uint32_t *d_out, uint64_t cap, uint64_t *n_out, uint64_t *n_candidates,
                                cudaStream_t st) {
     return guarded([&] { bm::frequent_triples(S, s, d_pairs, n_pairs, d_out, cap, n_out, n_candidates, st); });
+}
+
+batmap_status frequent_quadruples(batmap_set *S, uint32_t s, const uint32_t *d_triples, uint64_t n_triples,
+                                  uint32_t *d_out, uint64_t cap, uint64_t *n_out, uint64_t *n_candidates,
+                                  cudaStream_t st) {
+    return guarded(
+        [&] { bm::frequent_quadruples(S, s, d_triples, n_triples, d_out, cap, n_out, n_candidates, st); });
 }
 
 void batmap_free(batmap_set *set) {

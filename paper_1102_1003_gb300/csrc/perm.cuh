@@ -22,7 +22,7 @@
 
 namespace bm {
 
-constexpr int PERM_MAX_TABLES = 4;
+constexpr int PERM_MAX_TABLES = 5;  // d + 1 <= 5 (up to 4-of-5 BatMaps)
 
 struct PermView {
     const uint32_t *table;  // caller's rows pi_0.. of m entries each, or nullptr: computed
@@ -51,10 +51,10 @@ struct PermView {
         return (l << half) | r;
     }
 
-    // pi_t(x) for x < m (t < 3, or < 4 for 3-of-4 sets).
+    // pi_t(x) for x < m and t < PERM_MAX_TABLES (t < d + 1 of the set).
     __device__ __forceinline__ uint32_t operator()(uint32_t t, uint32_t x) const {
         if (table) return __ldg(&table[(uint64_t)t * m + x]);
-        const uint4 k = t == 0 ? key[0] : t == 1 ? key[1] : t == 2 ? key[2] : key[3];
+        const uint4 k = t == 0 ? key[0] : t == 1 ? key[1] : t == 2 ? key[2] : t == 3 ? key[3] : key[4];
         uint32_t v = pass(k, x);
         while (v >= m) v = pass(k, v);  // ends: x's own cycle returns below m
         return v;

@@ -1,6 +1,10 @@
 // d-of-(d+1) BatMaps and k-way supports (the generalisation that closes
-// Sec. V), and frequent itemsets of size 3 (the problem of Sec. I beyond
-// pairs, by the Apriori join-and-prune step over the frequent pairs).
+// Sec. V), and frequent itemsets of sizes 3 and 4 (the problem of Sec. I
+// beyond pairs, by the Apriori join-and-prune steps).
+//
+// d = 4 (4-of-5) follows the same pattern with five tables (block 5 r_0),
+// four copies per element, the missing table in bits 7..5 and a five-bit
+// code (m <= 31 * 2^s); the k-way rule (k <= 4) is witness_word5.
 //
 // Layout (d = 3): the BatMap of item i has four tables of r_i byte slots,
 // interleaved in blocks of r_0 as Sec. III-A interleaves three (block size
@@ -35,29 +39,48 @@ constexpr uint32_t TABLES = 4;  // d + 1
 constexpr uint32_t COPIES = 3;  // d
 constexpr uint32_t CODE_MASK = 0x3Fu;
 
-__host__ __device__ __forceinline__ uint64_t slot4(uint32_t t, uint32_t pi, uint32_t r, uint32_t shift) {
+// Field widths of a d-of-(d+1) byte over NT = d + 1 tables: the missing table
+// in the top bits, the code (pi >> s) + 1 in the rest (six code bits for four
+// tables, five for five).
+template <uint32_t NT>
+struct Fmt {
+    static constexpr uint32_t COPIES = NT - 1;
+    static constexpr uint32_t CODE_BITS = NT <= 4 ? 6u : 5u;
+    static constexpr uint32_t CODE_MASK = (1u << CODE_BITS) - 1u;
+    static constexpr uint32_t CODE_MAX = CODE_MASK;
+};
+
+// Slot of pi in table t: NT tables interleaved in blocks of r_0.
+template <uint32_t NT>
+__host__ __device__ __forceinline__ uint64_t slot_nt(uint32_t t, uint32_t pi, uint32_t r, uint32_t shift) {
     const uint32_t r0 = 1u << shift;
     const uint32_t h = pi & (r - 1u);
-    return 4ull * r0 * (uint64_t)(h >> shift) + (h & (r0 - 1u)) + (uint64_t)t * r0;
+    return (uint64_t)NT * r0 * (uint64_t)(h >> shift) + (h & (r0 - 1u)) + (uint64_t)t * r0;
+}
+
+__host__ __device__ __forceinline__ uint64_t slot4(uint32_t t, uint32_t pi, uint32_t r, uint32_t shift) {
+    return slot_nt<4>(t, pi, r, shift);
 }
 
 __device__ __forceinline__ uint32_t code6(uint32_t pi, uint32_t shift) { return (pi >> shift) + 1u; }
 
 // ---- build ------------------------------------------------------------------
 
-// Parallel INSERT with three copies: copy c of every element starts in table
-// c; a copy is swapped into its slot and the evicted occupant continues in
-// the next table (0, 1, 2, 3, 0, ...).  Swapping with another copy of the
-// same element leaves the slot unchanged and the element moves on, so copies
-// of one element never share a table.  A chain longer than max_moves drops
-// the copy it holds (the element then fails).
+// Parallel INSERT with d = NT - 1 copies: copy c of every element starts in
+// table c; a copy is swapped into its slot and the evicted occupant continues
+// in the next table (0, 1, .., NT - 1, 0, ...).  Swapping with another copy
+// of the same element leaves the slot unchanged and the element moves on, so
+// copies of one element never share a table.  A chain longer than max_moves
+// drops the copy it holds (the element then fails).
+template <uint32_t NT>
 __global__ void k_place(ItemView v, const PermView P, uint32_t shift, uint32_t max_moves,
                         uint32_t *__restrict__ table) {
+    constexpr uint32_t NC = Fmt<NT>::COPIES;
     const uint32_t m = P.m;
     uint32_t item;
     uint64_t e0, e1;
-    chunk_range(v, blockIdx.x / COPIES, &item, &e0, &e1);
-    const uint32_t copy = blockIdx.x % COPIES;
+    chunk_range(v, blockIdx.x / NC, &item, &e0, &e1);
+    const uint32_t copy = blockIdx.x % NC;
     const uint64_t base = v.base[item];
     const uint32_t r = 1u << v.rlog[item];
     for (uint64_t e = e0 + threadIdx.x; e < e1; e += TPB) {
@@ -66,34 +89,37 @@ __global__ void k_place(ItemView v, const PermView P, uint32_t shift, uint32_t m
         uint32_t t = copy;
         for (uint32_t mv = 0; mv < max_moves; mv++) {
             const uint32_t pi = P(t, x);
-            const uint32_t old = atomicExch(&table[base + slot4(t, pi, r, shift)], x);
+            const uint32_t old = atomicExch(&table[base + slot_nt<NT>(t, pi, r, shift)], x);
             if (old == EMPTY) break;
             x = old;
-            t = (t + 1u) & 3u;
+            t = (t + 1u == NT) ? 0u : t + 1u;
         }
     }
 }
 
-struct Copies4 {
-    uint32_t pi[TABLES];
-    uint64_t pos[TABLES];
+template <uint32_t NT>
+struct CopiesN {
+    uint32_t pi[NT];
+    uint64_t pos[NT];
     uint32_t has;  // bit t: a copy sits in table t
 };
 
-__device__ __forceinline__ Copies4 find_copies(uint32_t x, uint64_t base, uint32_t r, uint32_t shift,
-                                               const PermView &P, const uint32_t *__restrict__ table) {
-    Copies4 c;
+template <uint32_t NT>
+__device__ __forceinline__ CopiesN<NT> find_copies(uint32_t x, uint64_t base, uint32_t r, uint32_t shift,
+                                                   const PermView &P, const uint32_t *__restrict__ table) {
+    CopiesN<NT> c;
     c.has = 0;
 #pragma unroll
-    for (uint32_t t = 0; t < TABLES; t++) {
+    for (uint32_t t = 0; t < NT; t++) {
         c.pi[t] = P(t, x);
-        c.pos[t] = base + slot4(t, c.pi[t], r, shift);
+        c.pos[t] = base + slot_nt<NT>(t, c.pi[t], r, shift);
         if (table[c.pos[t]] == x) c.has |= 1u << t;
     }
     return c;
 }
 
-// Bytes of every element stored three times; failures counted per block.
+// Bytes of every element stored d times; failures counted per block.
+template <uint32_t NT>
 __global__ void k_finalize(ItemView v, const PermView P, uint32_t shift, const uint32_t *__restrict__ table,
                            uint8_t *__restrict__ out, uint64_t *__restrict__ blocksums) {
     const uint32_t m = P.m;
@@ -109,15 +135,16 @@ __global__ void k_finalize(ItemView v, const PermView P, uint32_t shift, const u
     for (uint64_t e = e0 + threadIdx.x; e < e1; e += TPB) {
         const uint32_t x = v.tids[e];
         if (x >= m) continue;
-        const Copies4 c = find_copies(x, base, r, shift, P, table);
-        if (__popc(c.has) != (int)COPIES) {
+        const CopiesN<NT> c = find_copies<NT>(x, base, r, shift, P, table);
+        if (__popc(c.has) != (int)Fmt<NT>::COPIES) {
             fails++;
             continue;
         }
-        const uint32_t missing = __ffs(~c.has & 0xFu) - 1;
+        const uint32_t missing = __ffs(~c.has & ((1u << NT) - 1u)) - 1;
 #pragma unroll
-        for (uint32_t t = 0; t < TABLES; t++)
-            if (c.has & (1u << t)) out[c.pos[t]] = (uint8_t)((missing << 6) | code6(c.pi[t], shift));
+        for (uint32_t t = 0; t < NT; t++)
+            if (c.has & (1u << t))
+                out[c.pos[t]] = (uint8_t)((missing << Fmt<NT>::CODE_BITS) | code6(c.pi[t], shift));
     }
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) fails += __shfl_xor_sync(0xffffffffu, fails, d);
@@ -128,6 +155,7 @@ __global__ void k_finalize(ItemView v, const PermView P, uint32_t shift, const u
 
 // Failed insertions in (item, tid) order: block offsets come from the scan
 // of the finalize counts.
+template <uint32_t NT>
 __global__ void k_failures(ItemView v, const PermView P, uint32_t shift, const uint32_t *__restrict__ table,
                            const uint64_t *blocksums, uint32_t *f_item, uint32_t *f_tid) {
     const uint32_t m = P.m;
@@ -144,7 +172,7 @@ __global__ void k_failures(ItemView v, const PermView P, uint32_t shift, const u
         uint32_t x = 0;
         if (e < e1) {
             x = v.tids[e];
-            fail = x < m && __popc(find_copies(x, base, r, shift, P, table).has) != (int)COPIES;
+            fail = x < m && __popc(find_copies<NT>(x, base, r, shift, P, table).has) != (int)Fmt<NT>::COPIES;
         }
         uint64_t tot;
         const uint64_t rank = block_exclusive_scan(fail ? 1 : 0, &tot);
@@ -156,17 +184,16 @@ __global__ void k_failures(ItemView v, const PermView P, uint32_t shift, const u
     }
 }
 
-static uint32_t shift_bits63(uint32_t m, uint32_t min_shift) {
+// Smallest s >= min_shift with m <= code_max * 2^s (codes 1..code_max, 0 = empty).
+static uint32_t shift_bits_codes(uint32_t m, uint32_t min_shift, uint32_t code_max) {
     uint32_t s = min_shift;
-    while ((uint64_t)m > 63ull << s) s++;
+    while ((uint64_t)m > (uint64_t)code_max << s) s++;
     return s;
 }
 
-}  // namespace wit
-
-void build_witness_set(batmap_set *S, const uint64_t *d_offsets, const uint32_t *d_tids,
-                       const uint32_t *d_perm) {
-    using namespace wit;
+template <uint32_t NT>
+void build_witness_impl(batmap_set *S, const uint64_t *d_offsets, const uint32_t *d_tids, const uint32_t *d_perm) {
+    constexpr uint32_t TABLES = NT, COPIES = Fmt<NT>::COPIES;
     std::lock_guard<std::mutex> scratch_lock(g_scratch_mu);
     const uint32_t m = S->m, n = S->n;
     cudaStream_t st = S->stream;
@@ -189,7 +216,7 @@ void build_witness_set(batmap_set *S, const uint64_t *d_offsets, const uint32_t 
     BM_REQUIRE(T == 0 || d_tids != nullptr, BATMAP_ERR_ARG, "d_tids is NULL");
 
     // ---- sizes: four tables of r_i slots; items keep their original order ----
-    S->shift = shift_bits63(m, P.min_shift);
+    S->shift = shift_bits_codes(m, P.min_shift, Fmt<NT>::CODE_MAX);
     S->r0 = 1u << S->shift;
     std::vector<uint32_t> rlog(n);
     std::vector<uint64_t> base(n + 1, 0);
@@ -198,7 +225,7 @@ void build_witness_set(batmap_set *S, const uint64_t *d_offsets, const uint32_t 
         rlog[i] = log2_range(off[i + 1] - off[i], P.load_num, P.load_den, S->shift);
         BM_REQUIRE(rlog[i] <= 30, BATMAP_ERR_ARG, "hash range exceeds 2^30");
         S->range[i] = 1u << rlog[i];
-        base[i + 1] = base[i] + (4ull << rlog[i]);
+        base[i + 1] = base[i] + ((uint64_t)TABLES << rlog[i]);
     }
     S->bytes = base[n];
     S->order.resize(n);
@@ -263,11 +290,11 @@ void build_witness_set(batmap_set *S, const uint64_t *d_offsets, const uint32_t 
         BM_CUDA(cudaMemsetAsync(table.p, 0xFF, S->bytes * sizeof(uint32_t), st));
         const uint32_t max_moves = TABLES * std::max<uint32_t>(P.max_loop, 1u);
         E.record(2, st);
-        k_place<<<COPIES * nch, TPB, 0, st>>>(v, PV, S->shift, max_moves, table.p);
+        k_place<NT><<<COPIES * nch, TPB, 0, st>>>(v, PV, S->shift, max_moves, table.p);
         BM_CHECK_LAUNCH();
         E.record(3, st);
         DevBuf<uint64_t> bs(nch + 1), d_tot(1);
-        k_finalize<<<nch, TPB, 0, st>>>(v, PV, S->shift, table.p, S->d_bm.p, bs.p);
+        k_finalize<NT><<<nch, TPB, 0, st>>>(v, PV, S->shift, table.p, S->d_bm.p, bs.p);
         BM_CHECK_LAUNCH();
         k_scan_single_block<<<1, SCAN_TPB, 0, st>>>(bs.p, nch, d_tot.p, 1);
         BM_CHECK_LAUNCH();
@@ -278,7 +305,7 @@ void build_witness_set(batmap_set *S, const uint64_t *d_offsets, const uint32_t 
         DevBuf<uint32_t> f_item(nfail);
         S->d_fail_tid.alloc(nfail);
         if (nfail) {
-            k_failures<<<nch, TPB, 0, st>>>(v, PV, S->shift, table.p, bs.p, f_item.p,
+            k_failures<NT><<<nch, TPB, 0, st>>>(v, PV, S->shift, table.p, bs.p, f_item.p,
                                             S->d_fail_tid.p);
             BM_CHECK_LAUNCH();
         }
@@ -296,6 +323,14 @@ void build_witness_set(batmap_set *S, const uint64_t *d_offsets, const uint32_t 
     S->timing.build_ms = E.ms(0, 1);
     S->timing.place_ms = E.ms(2, 3);
     S->timing.finalize_ms = E.ms(3, 4);
+}
+
+}  // namespace wit
+
+// d-of-(d+1) build for d = 3 (3-of-4) and d = 4 (4-of-5).
+void build_witness_set(batmap_set *S, const uint64_t *d_offsets, const uint32_t *d_tids, const uint32_t *d_perm) {
+    if (S->d == 4) wit::build_witness_impl<5>(S, d_offsets, d_tids, d_perm);
+    else wit::build_witness_impl<4>(S, d_offsets, d_tids, d_perm);
 }
 
 namespace wit {
@@ -340,15 +375,40 @@ __device__ __forceinline__ uint32_t witness_word(const uint32_t (&x)[K], uint32_
     return __popc(ok);
 }
 
-// x is stored in item's BatMap: a copy sits in table 0 or table 1 (three of
-// four tables hold one), recognised by its code at h_t(x).
+// The same rule over five tables (d = 4): five code bits, the missing table
+// in bits 7..5.  A lane counts iff the K codes agree and are nonzero and
+// every table u < t is missed by some set (then t, which the K copies occupy,
+// is the smallest table missed by none).
+template <int K>
+__device__ __forceinline__ uint32_t witness_word5(const uint32_t (&x)[K], uint32_t t) {
+    constexpr uint32_t C5 = 0x1F1F1F1Fu, K7 = 0x7F7F7F7Fu, H7 = 0x80808080u, M3 = 0xE0E0E0E0u;
+    uint32_t diff = 0;
+#pragma unroll
+    for (int j = 1; j < K; j++) diff |= x[0] ^ x[j];
+    // bit 7 of (v + 0x7F..) flags a nonzero lane of v <= 0x1F (no carry leaves a lane)
+    const uint32_t ne = ((diff & C5) + K7) & H7;  // codes differ somewhere
+    const uint32_t nz = ((x[0] & C5) + K7) & H7;  // slot not empty
+    uint32_t ok = nz & ~ne;
+    for (uint32_t u = 0; u < t; u++) {
+        const uint32_t U = u * 0x20202020u;  // u in bits 7..5 of every lane
+        uint32_t e = 0;                       // bit 7: some set misses table u
+#pragma unroll
+        for (int j = 0; j < K; j++) e |= ~((((x[j] ^ U) & M3) >> 5) + K7);
+        ok &= e;
+    }
+    return __popc(ok & H7);
+}
+
+// x is stored in item's BatMap: a copy sits in table 0 or table 1 (d of the
+// d + 1 tables hold one), recognised by its code at h_t(x).
+template <uint32_t NT>
 __device__ __forceinline__ bool stored_in(const View &V, uint32_t item, uint32_t x) {
     const uint32_t r = 1u << V.rlog[item];
     const uint8_t *b = reinterpret_cast<const uint8_t *>(V.bm) + V.base[item];
 #pragma unroll
     for (uint32_t t = 0; t < 2; t++) {
         const uint32_t pi = V.perm(t, x);
-        if ((b[slot4(t, pi, r, V.shift)] & CODE_MASK) == code6(pi, V.shift)) return true;
+        if ((b[slot_nt<NT>(t, pi, r, V.shift)] & Fmt<NT>::CODE_MASK) == code6(pi, V.shift)) return true;
     }
     return false;
 }
@@ -367,7 +427,7 @@ __device__ __forceinline__ bool failed_in(const View &V, uint32_t item, uint32_t
 // The lane's share of the failed common elements of the K sets: x from F of
 // set j counts unless an earlier set i < j also failed it (then it is
 // counted from set i's list).
-template <int K>
+template <int K, uint32_t NT>
 __device__ __forceinline__ uint32_t failed_common(const View &V, const uint32_t (&it)[K], uint32_t lane) {
     uint32_t cnt = 0;
 #pragma unroll
@@ -381,7 +441,7 @@ __device__ __forceinline__ uint32_t failed_common(const View &V, const uint32_t 
                 if (i == j || !all) continue;
                 const bool fi = failed_in(V, it[i], x);
                 if (i < j && fi) all = false;
-                else all = fi || stored_in(V, it[i], x);
+                else all = fi || stored_in<NT>(V, it[i], x);
             }
             cnt += all ? 1u : 0u;
         }
@@ -389,35 +449,40 @@ __device__ __forceinline__ uint32_t failed_common(const View &V, const uint32_t 
     return cnt;
 }
 
-// One warp per query of K item ids.  Lane l reads word w = w0 + l of every
-// BatMap, the narrower ones cyclically (w mod r_i); 32 consecutive words lie
+// One warp per query of K item ids on a set of NT = d + 1 tables.  Lane l
+// reads word w = w0 + l of every BatMap, the narrower ones cyclically (w mod
+// the width NT r_i / 4 words: block-wise, Fig. 1); 32 consecutive words lie
 // in one table because a table block is r_0 >= 128 bytes.
-template <int K>
+template <int K, uint32_t NT>
 __global__ void __launch_bounds__(256) k_witness(View V, const uint32_t *__restrict__ items, uint64_t nq,
                                                  uint32_t *__restrict__ out) {
     const uint32_t lane = threadIdx.x & 31u;
     const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x / 32);
     for (uint64_t q = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) / 32; q < nq; q += nwarps) {
-        uint32_t it[K], mask[K];
+        uint32_t it[K], e[K];
         uint64_t wb[K];
-        uint32_t rmax = 0;
+        uint32_t wmax = 0;
 #pragma unroll
         for (int j = 0; j < K; j++) {
             it[j] = __ldg(&items[q * K + j]);
-            const uint32_t r = 1u << V.rlog[it[j]];
-            mask[j] = r - 1u;
+            e[j] = V.rlog[it[j]] - 2;  // 2^e words per table segment of a block run
             wb[j] = V.base[it[j]] >> 2;
-            rmax = r > rmax ? r : rmax;
+            wmax = max(wmax, NT << e[j]);
         }
         const uint32_t tshift = V.shift - 2;  // words per table block = r_0 / 4
         uint32_t cnt = 0;
-        for (uint32_t w = lane; w < rmax; w += 32) {
+        for (uint32_t w = lane; w < wmax; w += 32) {
             uint32_t x[K];
 #pragma unroll
-            for (int j = 0; j < K; j++) x[j] = __ldg(&V.bm[wb[j] + (w & mask[j])]);
-            cnt += witness_word<K>(x, (w >> tshift) & 3u);
+            for (int j = 0; j < K; j++) {
+                const uint32_t wj = ((w >> e[j]) % NT) << e[j] | (w & ((1u << e[j]) - 1u));
+                x[j] = __ldg(&V.bm[wb[j] + wj]);
+            }
+            const uint32_t t = (w >> tshift) % NT;
+            if constexpr (NT == 4) cnt += witness_word<K>(x, t);
+            else cnt += witness_word5<K>(x, t);
         }
-        cnt += failed_common<K>(V, it, lane);
+        cnt += failed_common<K, NT>(V, it, lane);
 #pragma unroll
         for (int d = 16; d > 0; d >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, d);
         if (lane == 0) out[q] = cnt;
@@ -627,7 +692,7 @@ __global__ void __launch_bounds__(WG_TPB) k_witness_group(View V, const uint32_t
             if (j >= gn) break;  // unused slots (klim = 0) sort last
             const uint32_t o = (pos >> (4 * j)) & 15u;
             const uint32_t it[3] = {a, b, cand[3 * (c0 + o) + 2]};
-            uint32_t v = cnt[j] + failed_common<3>(V, it, lane);
+            uint32_t v = cnt[j] + failed_common<3, 4>(V, it, lane);
 #pragma unroll
             for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
             if (lane == 0) sup[c0 + o] = v;
@@ -696,11 +761,12 @@ __global__ void k_candidates(const uint32_t *__restrict__ pairs, uint64_t np, co
     }
 }
 
-// Ordered compaction of the candidates with support >= s into (a, b, c, support).
+// Ordered compaction of the K-item candidates with support >= s into
+// (item_1, .., item_K, support).
 constexpr int TH_PER = 8;
-template <bool WRITE>
-__global__ void k_triple_threshold(const uint32_t *__restrict__ cand, const uint32_t *__restrict__ sup, uint64_t nc,
-                                   uint32_t s, uint64_t *blocksums, uint32_t *__restrict__ out, uint64_t cap) {
+template <int K, bool WRITE>
+__global__ void k_tuple_threshold(const uint32_t *__restrict__ cand, const uint32_t *__restrict__ sup, uint64_t nc,
+                                  uint32_t s, uint64_t *blocksums, uint32_t *__restrict__ out, uint64_t cap) {
     const uint64_t b0 = (uint64_t)blockIdx.x * SCAN_TPB * TH_PER;
     uint64_t running = WRITE ? blocksums[blockIdx.x] : 0;
     for (int j = 0; j < TH_PER; j++) {
@@ -709,25 +775,99 @@ __global__ void k_triple_threshold(const uint32_t *__restrict__ cand, const uint
         uint64_t tot;
         const uint64_t rank = block_exclusive_scan(keep ? 1 : 0, &tot);
         if (WRITE && keep && running + rank < cap) {
-            const uint64_t o = 4 * (running + rank);
-            out[o] = cand[3 * c];
-            out[o + 1] = cand[3 * c + 1];
-            out[o + 2] = cand[3 * c + 2];
-            out[o + 3] = sup[c];
+            const uint64_t o = (K + 1) * (running + rank);
+#pragma unroll
+            for (int q = 0; q < K; q++) out[o + q] = cand[(uint64_t)K * c + q];
+            out[o + K] = sup[c];
         }
         running += tot;
     }
     if (!WRITE && threadIdx.x == 0) blocksums[blockIdx.x] = running;
 }
 
+// ---- Apriori level 4 ------------------------------------------------------------
+
+// Frequent triples (a, b, c, support), a < b < c < n, lexicographic: err <- 1
+// unless the list is strictly increasing with ids < n.
+__global__ void k_check_triples(const uint32_t *t3, uint64_t nt, uint32_t n, int *err) {
+    for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < nt;
+         p += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t a = t3[4 * p], b = t3[4 * p + 1], c = t3[4 * p + 2];
+        bool bad = !(a < b && b < c) || c >= n;
+        if (p + 1 < nt) {
+            const uint32_t a2 = t3[4 * p + 4], b2 = t3[4 * p + 5], c2 = t3[4 * p + 6];
+            bad |= !(a < a2 || (a == a2 && (b < b2 || (b == b2 && c < c2))));
+        }
+        if (bad) atomicExch(err, 1);
+    }
+}
+
+// Is (a, b, c) one of the nt lexicographic triples?  (binary search)
+__device__ __forceinline__ bool has_triple(const uint32_t *t3, uint64_t nt, uint32_t a, uint32_t b, uint32_t c) {
+    uint64_t lo = 0, hi = nt;
+    while (lo < hi) {
+        const uint64_t mid = (lo + hi) >> 1;
+        const uint32_t x = t3[4 * mid], y = t3[4 * mid + 1], z = t3[4 * mid + 2];
+        const bool less = x < a || (x == a && (y < b || (y == b && z < c)));
+        if (less) lo = mid + 1; else hi = mid;
+    }
+    return lo < nt && t3[4 * lo] == a && t3[4 * lo + 1] == b && t3[4 * lo + 2] == c;
+}
+
+// For the frequent triple p = (a, b, c): every d > c with (a, b, d) frequent
+// (the later triples of p's (a, b) run) whose other 3-subsets (a, c, d) and
+// (b, c, d) are frequent too.  COUNT writes the number into cnt[p]; otherwise
+// the quadruples are written from offset cnt[p].
+template <bool WRITE>
+__global__ void k_quad_candidates(const uint32_t *__restrict__ t3, uint64_t nt, uint64_t *cnt,
+                                  uint32_t *__restrict__ out) {
+    for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < nt;
+         p += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t a = t3[4 * p], b = t3[4 * p + 1], c = t3[4 * p + 2];
+        uint64_t k = WRITE ? cnt[p] : 0;
+        for (uint64_t q = p + 1; q < nt && t3[4 * q] == a && t3[4 * q + 1] == b; q++) {
+            const uint32_t d = t3[4 * q + 2];
+            if (has_triple(t3, nt, a, c, d) && has_triple(t3, nt, b, c, d)) {
+                if (WRITE) {
+                    out[4 * k] = a;
+                    out[4 * k + 1] = b;
+                    out[4 * k + 2] = c;
+                    out[4 * k + 3] = d;
+                }
+                k++;
+            }
+        }
+        if (!WRITE) cnt[p] = k;
+    }
+}
+
 }  // namespace wit
 
-// Supports of n_q queries of k item ids each (k in 1..3) on a 3-of-4 set.
+// One warp per query: k ids each, on a set of d + 1 tables.
+static void launch_witness(const wit::View &V, uint32_t d, uint32_t k, const uint32_t *d_items, uint64_t nq,
+                           uint32_t *d_support, cudaStream_t st) {
+    using namespace wit;
+    if (nq == 0) return;
+    const unsigned grid = (unsigned)std::min<uint64_t>((nq + 7) / 8, 152ull * 64);
+    if (d == 3) {
+        if (k == 1) k_witness<1, 4><<<grid, 256, 0, st>>>(V, d_items, nq, d_support);
+        if (k == 2) k_witness<2, 4><<<grid, 256, 0, st>>>(V, d_items, nq, d_support);
+        if (k == 3) k_witness<3, 4><<<grid, 256, 0, st>>>(V, d_items, nq, d_support);
+    } else {
+        if (k == 1) k_witness<1, 5><<<grid, 256, 0, st>>>(V, d_items, nq, d_support);
+        if (k == 2) k_witness<2, 5><<<grid, 256, 0, st>>>(V, d_items, nq, d_support);
+        if (k == 3) k_witness<3, 5><<<grid, 256, 0, st>>>(V, d_items, nq, d_support);
+        if (k == 4) k_witness<4, 5><<<grid, 256, 0, st>>>(V, d_items, nq, d_support);
+    }
+    BM_CHECK_LAUNCH();
+}
+
+// Supports of n_q queries of k item ids each (k in 1..d) on a d-of-(d+1) set.
 void witness_support(batmap_set *S, uint32_t k, uint64_t nq, const uint32_t *d_items, uint32_t *d_support,
                      cudaStream_t st) {
     using namespace wit;
-    BM_REQUIRE(S && S->d == 3, BATMAP_ERR_ARG, "itemset supports need a set built with d = 3");
-    BM_REQUIRE(k >= 1 && k <= 3, BATMAP_ERR_ARG, "k must be 1, 2 or 3");
+    BM_REQUIRE(S && (S->d == 3 || S->d == 4), BATMAP_ERR_ARG, "itemset supports need a set built with d = 3 or 4");
+    BM_REQUIRE(k >= 1 && k <= S->d, BATMAP_ERR_ARG, "k must be in 1..d");
     if (nq == 0) return;
     BM_REQUIRE(d_items && d_support, BATMAP_ERR_ARG, "NULL argument");
     {
@@ -742,11 +882,7 @@ void witness_support(batmap_set *S, uint32_t k, uint64_t nq, const uint32_t *d_i
     }
     const View V{reinterpret_cast<const uint32_t *>(S->d_bm.p), S->d_base.p, S->d_rlog.p, S->perm,
                  S->d_fail_off.p, S->d_fail_tid.p, S->m, S->n, S->shift};
-    const unsigned grid = (unsigned)std::min<uint64_t>((nq + 7) / 8, 152ull * 64);
-    if (k == 1) k_witness<1><<<grid, 256, 0, st>>>(V, d_items, nq, d_support);
-    if (k == 2) k_witness<2><<<grid, 256, 0, st>>>(V, d_items, nq, d_support);
-    if (k == 3) k_witness<3><<<grid, 256, 0, st>>>(V, d_items, nq, d_support);
-    BM_CHECK_LAUNCH();
+    launch_witness(V, S->d, k, d_items, nq, d_support, st);
 }
 
 // Frequent itemsets of size 3 from the frequent pairs (Apriori join and
@@ -754,7 +890,8 @@ void witness_support(batmap_set *S, uint32_t k, uint64_t nq, const uint32_t *d_i
 void frequent_triples(batmap_set *S, uint32_t s, const uint32_t *d_pairs, uint64_t np, uint32_t *d_out,
                       uint64_t cap, uint64_t *n_out, uint64_t *n_cand, cudaStream_t st) {
     using namespace wit;
-    BM_REQUIRE(S && S->d == 3, BATMAP_ERR_ARG, "frequent_triples needs a set built with d = 3");
+    BM_REQUIRE(S && (S->d == 3 || S->d == 4), BATMAP_ERR_ARG, "frequent_triples needs a set built with d = 3 or 4");
+    const bool grouped = S->d == 3;  // the grouped kernel reads the 3-of-4 format
     BM_REQUIRE(n_out, BATMAP_ERR_ARG, "n_out is NULL");
     BM_REQUIRE(np == 0 || d_pairs, BATMAP_ERR_ARG, "d_pairs is NULL");
     BM_REQUIRE(cap == 0 || d_out, BATMAP_ERR_ARG, "d_out is NULL with cap > 0");
@@ -790,6 +927,8 @@ void frequent_triples(batmap_set *S, uint32_t s, const uint32_t *d_pairs, uint64
         if (nc) {
             k_candidates<true><<<grid_for(np), 256, 0, st>>>(d_pairs, np, row_off.p, cnt.p, cand.p);
             BM_CHECK_LAUNCH();
+        }
+        if (nc && grouped) {
             // work units of up to GROUP candidates sharing their frequent pair
             DevBuf<uint64_t> uoff(np + 1), utot(1);
             k_unit_counts<<<grid_for(np), 256, 0, st>>>(cnt.p, np, uoff.p);
@@ -810,10 +949,14 @@ void frequent_triples(batmap_set *S, uint32_t s, const uint32_t *d_pairs, uint64
     if (nc) {
         const View V{reinterpret_cast<const uint32_t *>(S->d_bm.p), S->d_base.p, S->d_rlog.p, S->perm,
                      S->d_fail_off.p, S->d_fail_tid.p, S->m, S->n, S->shift};
-        const uint64_t wpb = WG_TPB / 32;
-        const unsigned grid = (unsigned)std::min<uint64_t>((n_units + wpb - 1) / wpb, 152ull * 64);
-        k_witness_group<<<grid, WG_TPB, 0, st>>>(V, d_pairs, cnt.p, cand.p, units.p, n_units, sup.p);
-        BM_CHECK_LAUNCH();
+        if (grouped) {
+            const uint64_t wpb = WG_TPB / 32;
+            const unsigned grid = (unsigned)std::min<uint64_t>((n_units + wpb - 1) / wpb, 152ull * 64);
+            k_witness_group<<<grid, WG_TPB, 0, st>>>(V, d_pairs, cnt.p, cand.p, units.p, n_units, sup.p);
+            BM_CHECK_LAUNCH();
+        } else {
+            launch_witness(V, S->d, 3, cand.p, nc, sup.p, st);  // one warp per candidate
+        }
     }
     E.record(2, st);
     uint64_t total = 0;
@@ -821,11 +964,11 @@ void frequent_triples(batmap_set *S, uint32_t s, const uint32_t *d_pairs, uint64
         const uint64_t per_block = (uint64_t)SCAN_TPB * TH_PER;
         const uint64_t nb = (nc + per_block - 1) / per_block;
         DevBuf<uint64_t> bs(nb + 1), tot(1);
-        k_triple_threshold<false><<<(unsigned)nb, SCAN_TPB, 0, st>>>(cand.p, sup.p, nc, s, bs.p, nullptr, 0);
+        k_tuple_threshold<3, false><<<(unsigned)nb, SCAN_TPB, 0, st>>>(cand.p, sup.p, nc, s, bs.p, nullptr, 0);
         BM_CHECK_LAUNCH();
         k_scan_single_block<<<1, SCAN_TPB, 0, st>>>(bs.p, nb, tot.p, 1);
         BM_CHECK_LAUNCH();
-        k_triple_threshold<true><<<(unsigned)nb, SCAN_TPB, 0, st>>>(cand.p, sup.p, nc, s, bs.p, d_out, cap);
+        k_tuple_threshold<3, true><<<(unsigned)nb, SCAN_TPB, 0, st>>>(cand.p, sup.p, nc, s, bs.p, d_out, cap);
         BM_CHECK_LAUNCH();
         BM_CUDA(cudaMemcpyAsync(&total, tot.p, 8, cudaMemcpyDeviceToHost, st));
     }
@@ -837,6 +980,75 @@ void frequent_triples(batmap_set *S, uint32_t s, const uint32_t *d_pairs, uint64
     *n_out = total;
     if (total > cap)
         throw Error{BATMAP_ERR_CAPACITY, "d_out too small: " + std::to_string(total) + " triples qualify"};
+}
+
+// Frequent itemsets of size 4 from the frequent triples (Apriori join of the
+// triples sharing (a, b), pruned by the other two 3-subsets), supports by the
+// five-table witness rule, compaction in lexicographic order.
+void frequent_quadruples(batmap_set *S, uint32_t s, const uint32_t *d_triples, uint64_t nt, uint32_t *d_out,
+                         uint64_t cap, uint64_t *n_out, uint64_t *n_cand, cudaStream_t st) {
+    using namespace wit;
+    BM_REQUIRE(S && S->d == 4, BATMAP_ERR_ARG, "frequent_quadruples needs a set built with d = 4");
+    BM_REQUIRE(n_out, BATMAP_ERR_ARG, "n_out is NULL");
+    BM_REQUIRE(nt == 0 || d_triples, BATMAP_ERR_ARG, "d_triples is NULL");
+    BM_REQUIRE(cap == 0 || d_out, BATMAP_ERR_ARG, "d_out is NULL with cap > 0");
+    PhaseEvents &E = S->pairs_ev;
+    E.create();
+    E.record(0, st);
+    uint64_t nc = 0;
+    DevBuf<uint32_t> cand, sup;
+    if (nt) {
+        DevBuf<int> err(1);
+        DevBuf<uint64_t> cnt(nt + 1), tot(1);
+        BM_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
+        k_check_triples<<<grid_for(nt), 256, 0, st>>>(d_triples, nt, S->n, err.p);
+        BM_CHECK_LAUNCH();
+        int h = 0;
+        BM_CUDA(cudaMemcpyAsync(&h, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        BM_CUDA(cudaStreamSynchronize(st));
+        BM_REQUIRE(h == 0, BATMAP_ERR_ARG, "triples must be (a, b, c, support) with a < b < c < n, lexicographic");
+        k_quad_candidates<false><<<grid_for(nt), 256, 0, st>>>(d_triples, nt, cnt.p, nullptr);
+        BM_CHECK_LAUNCH();
+        k_scan_single_block<<<1, SCAN_TPB, 0, st>>>(cnt.p, nt, tot.p, 1);
+        BM_CHECK_LAUNCH();
+        BM_CUDA(cudaMemcpyAsync(&nc, tot.p, 8, cudaMemcpyDeviceToHost, st));
+        BM_CUDA(cudaStreamSynchronize(st));
+        cand.alloc(4 * nc);
+        sup.alloc(nc);
+        if (nc) {
+            k_quad_candidates<true><<<grid_for(nt), 256, 0, st>>>(d_triples, nt, cnt.p, cand.p);
+            BM_CHECK_LAUNCH();
+        }
+    }
+    if (n_cand) *n_cand = nc;
+    E.record(1, st);
+    if (nc) {
+        const View V{reinterpret_cast<const uint32_t *>(S->d_bm.p), S->d_base.p, S->d_rlog.p, S->perm,
+                     S->d_fail_off.p, S->d_fail_tid.p, S->m, S->n, S->shift};
+        launch_witness(V, 4, 4, cand.p, nc, sup.p, st);
+    }
+    E.record(2, st);
+    uint64_t total = 0;
+    if (nc) {
+        const uint64_t per_block = (uint64_t)SCAN_TPB * TH_PER;
+        const uint64_t nb = (nc + per_block - 1) / per_block;
+        DevBuf<uint64_t> bs(nb + 1), tot(1);
+        k_tuple_threshold<4, false><<<(unsigned)nb, SCAN_TPB, 0, st>>>(cand.p, sup.p, nc, s, bs.p, nullptr, 0);
+        BM_CHECK_LAUNCH();
+        k_scan_single_block<<<1, SCAN_TPB, 0, st>>>(bs.p, nb, tot.p, 1);
+        BM_CHECK_LAUNCH();
+        k_tuple_threshold<4, true><<<(unsigned)nb, SCAN_TPB, 0, st>>>(cand.p, sup.p, nc, s, bs.p, d_out, cap);
+        BM_CHECK_LAUNCH();
+        BM_CUDA(cudaMemcpyAsync(&total, tot.p, 8, cudaMemcpyDeviceToHost, st));
+    }
+    E.record(3, st);
+    BM_CUDA(cudaStreamSynchronize(st));
+    S->timing.compare_ms = E.ms(1, 2);
+    S->timing.compact_ms = E.ms(0, 1) + E.ms(2, 3);
+    S->timing.pairs_ms = E.ms(0, 3);
+    *n_out = total;
+    if (total > cap)
+        throw Error{BATMAP_ERR_CAPACITY, "d_out too small: " + std::to_string(total) + " quadruples qualify"};
 }
 
 }  // namespace bm
