@@ -112,7 +112,14 @@ struct Tile {
     static constexpr int ROW_CHUNKS = TR * CPR;
     static constexpr int COL_CHUNKS = TC * CPR;
     static constexpr int STAGE_CHUNKS = ROW_CHUNKS + COL_CHUNKS;
-    static constexpr size_t SMEM = (size_t)STAGES * STAGE_CHUNKS * 16;
+    // Shapes with three stages keep a second, masked copy of two stages
+    // (indicator bits only, x & 0x80808080), written once per stage: the
+    // compare loop reads the masks instead of forming them for every
+    // register-tile word, which takes (8 + MC) / (8 MC) logic instructions
+    // per word pair off the ALU pipe.
+    static constexpr bool MASKED = STAGES >= 3;
+    static constexpr int MASK_BUFS = MASKED ? 2 : 0;
+    static constexpr size_t SMEM = (size_t)(STAGES + MASK_BUFS) * STAGE_CHUNKS * 16;
     static_assert(NT == 256, "256 threads per CTA");
 
     __device__ static __forceinline__ int sw(int r, int kq) {
@@ -160,40 +167,76 @@ __device__ __forceinline__ void process_unit(uint4 *smem, const InstView &V, con
 #pragma unroll
         for (int b = 0; b < MC; b++) acc[a][b] = 0;
 
+    // masked copy of stage `stage` (same positions as its raw copy)
+    uint4 *const mring = smem + (size_t)STAGES * T::STAGE_CHUNKS;
+    auto mask_stage = [&](uint32_t stage) {
+        const uint4 *src = smem + (size_t)(stage % STAGES) * T::STAGE_CHUNKS;
+        uint4 *dst = mring + (size_t)(stage & 1u) * T::STAGE_CHUNKS;
+        for (int q = tid; q < T::STAGE_CHUNKS; q += T::NT) {
+            const uint4 v = src[q];
+            dst[q] = make_uint4(v.x & 0x80808080u, v.y & 0x80808080u, v.z & 0x80808080u, v.w & 0x80808080u);
+        }
+    };
+
+    // Copy groups: one per stage.  Unmasked: stage s is waited for in
+    // iteration s.  Masked: stage s+1 is waited for in iteration s, which then
+    // masks it (into mask buffer (s+1) & 1) while stage s is compared; the
+    // barrier of iteration s publishes stage s+1 and the masks of stage s, and
+    // retires every read of stage s-1 (whose raw buffer the fill of stage s+2
+    // and whose mask buffer the masks of stage s+1 overwrite).
 #pragma unroll
     for (int s = 0; s < STAGES - 1; s++) {
         if ((uint32_t)s < nst) fill(s, s);
         cp_async_commit();
     }
-    for (uint32_t s = 0; s < nst; s++) {
+    if constexpr (T::MASKED) {
         cp_async_wait<STAGES - 2>();
+        __syncthreads();
+        if (nst) mask_stage(0);
+    }
+    for (uint32_t s = 0; s < nst; s++) {
+        if constexpr (T::MASKED) cp_async_wait<0>(); else cp_async_wait<STAGES - 2>();
         __syncthreads();
         {
             uint32_t nxt = s + STAGES - 1;
             if (nxt < nst) fill(nxt, nxt % STAGES);
             cp_async_commit();
         }
+        if constexpr (T::MASKED) {
+            if (s + 1 < nst) mask_stage(s + 1);
+        }
         const uint4 *rows = smem + (size_t)(s % STAGES) * T::STAGE_CHUNKS;
         const uint4 *cols = rows + T::ROW_CHUNKS;
+        const uint4 *mrows = mring + (size_t)(s & 1u) * T::STAGE_CHUNKS;
+        const uint4 *mcols = mrows + T::ROW_CHUNKS;
 #pragma unroll 1
         for (int kq = 0; kq < T::CPR; kq++) {
-            uint4 X[8], Y[MC];
+            uint4 X[8], Y[MC], XI[T::MASKED ? 8 : 1], YI[T::MASKED ? MC : 1];
 #pragma unroll
-            for (int a = 0; a < 8; a++) X[a] = rows[T::sw(tr + TR_T * a, kq)];
+            for (int a = 0; a < 8; a++) {
+                X[a] = rows[T::sw(tr + TR_T * a, kq)];
+                if constexpr (T::MASKED) XI[a] = mrows[T::sw(tr + TR_T * a, kq)];
+            }
 #pragma unroll
-            for (int b = 0; b < MC; b++) Y[b] = cols[T::sw(tc + TC_T * b, kq)];
+            for (int b = 0; b < MC; b++) {
+                Y[b] = cols[T::sw(tc + TC_T * b, kq)];
+                if constexpr (T::MASKED) YI[b] = mcols[T::sw(tc + TC_T * b, kq)];
+            }
 #pragma unroll
             for (int kk = 0; kk < 4; kk++) {
                 uint32_t yw[MC], yi[MC];
 #pragma unroll
                 for (int b = 0; b < MC; b++) {
                     yw[b] = lane_word(Y[b], kk);
-                    yi[b] = yw[b] & 0x80808080u;
+                    if constexpr (T::MASKED) yi[b] = lane_word(YI[b], kk);
+                    else yi[b] = yw[b] & 0x80808080u;
                 }
 #pragma unroll
                 for (int a = 0; a < 8; a++) {
                     const uint32_t xw = lane_word(X[a], kk);
-                    const uint32_t xi = xw & 0x80808080u;
+                    uint32_t xi;
+                    if constexpr (T::MASKED) xi = lane_word(XI[a], kk);
+                    else xi = xw & 0x80808080u;
 #pragma unroll
                     for (int b = 0; b < MC; b++) acc[a][b] = swar_step(acc[a][b], xw, xi, yw[b], yi[b]);
                 }
