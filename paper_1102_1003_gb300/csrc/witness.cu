@@ -509,6 +509,106 @@ constexpr uint32_t GROUP = 8;
 constexpr uint32_t WG_TPB = 128;  // threads per block of k_witness_group
 static_assert(GROUP <= 8, "a unit's slot order is kept in four bits per slot of one word");
 
+// Width-skewed candidates go to the probe kernel instead of the scan: when
+// the widest of the three BatMaps is at least 2^PROBE_LOG times the
+// narrowest, the scan (which runs over the widest) costs more than visiting
+// the narrowest one's slots and probing the other two.
+constexpr uint32_t PROBE_LOG = 3;
+__device__ __forceinline__ bool probe_route(uint32_t la, uint32_t lb, uint32_t lc) {
+    return max(max(la, lb), lc) - min(min(la, lb), lc) >= PROBE_LOG;
+}
+
+// Indices of the candidates routed to the probe kernel (any order).
+__global__ void k_route_probe(const uint32_t *__restrict__ cand, uint64_t nc, const uint32_t *__restrict__ rlog,
+                              uint32_t *__restrict__ list, unsigned long long *__restrict__ count) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nc; i += (uint64_t)gridDim.x * blockDim.x)
+        if (probe_route(rlog[cand[3 * i]], rlog[cand[3 * i + 1]], rlog[cand[3 * i + 2]]))
+            list[atomicAdd(count, 1ull)] = (uint32_t)i;
+}
+
+// Triple supports by probing (the second k-way idea of Sec. V: look up the
+// elements of the smallest set in the others), on 3-of-4 BatMaps.  A
+// nonempty slot of the narrowest BatMap in table t at byte h holds a copy of
+// some x with pi_t(x) = ((code - 1) << s) | (h mod r_0): the code gives the
+// bits above s and the slot the bits below.  The other two sets hold x in
+// table t iff the byte at their slot for pi_t(x) carries the same code (slot
+// and code together fix pi_t(x), and pi_t is a bijection).  Counting the copy
+// only where all three hold x in t and t is the smallest table none of the
+// three misses counts every element stored in all three once, as the scan's
+// witness rule does; elements failed in any of them come from their F lists.
+// One warp per routed candidate; lanes take the narrowest BatMap's words.
+__global__ void __launch_bounds__(256) k_witness_probe(View V, const uint32_t *__restrict__ cand,
+                                                       const uint32_t *__restrict__ list,
+                                                       const unsigned long long *__restrict__ count,
+                                                       uint32_t *__restrict__ sup) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x / 32);
+    const uint64_t np = *count;
+    const uint32_t s = V.shift, r0m = (1u << s) - 1u;
+    const uint8_t *bytes = reinterpret_cast<const uint8_t *>(V.bm);
+    __shared__ uint32_t s_slots[8][512];  // per warp: the nonempty slots of 32 chunks
+    uint32_t *slots = s_slots[threadIdx.x >> 5];
+    for (uint64_t q = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) / 32; q < np; q += nwarps) {
+        const uint32_t i = list[q];
+        const uint32_t it[3] = {cand[3ull * i], cand[3ull * i + 1], cand[3ull * i + 2]};
+        const uint32_t l0 = V.rlog[it[0]], l1 = V.rlog[it[1]], l2 = V.rlog[it[2]];
+        // narrowest set n0 (log range ln) and the other two, o1 and o2
+        const bool first = l0 <= l1 && l0 <= l2, second = !first && l1 <= l2;
+        const uint32_t n0 = first ? it[0] : second ? it[1] : it[2];
+        const uint32_t ln = first ? l0 : second ? l1 : l2;
+        const uint32_t o1 = first ? it[1] : it[0], lo1 = first ? l1 : l0;
+        const uint32_t o2 = (first || second) ? it[2] : it[1], lo2 = (first || second) ? l2 : l1;
+        const uint32_t r1 = 1u << lo1, r2 = 1u << lo2;
+        const uint32_t *w0 = V.bm + (V.base[n0] >> 2);
+        const uint8_t *b1 = bytes + V.base[o1], *b2 = bytes + V.base[o2];
+        const uint32_t words = 1u << ln;  // 4 r bytes of the narrowest BatMap
+        // Lanes read 16-byte chunks of the narrowest BatMap; the warp packs its
+        // nonempty slots (byte offset << 8 | byte) into shared memory by a
+        // prefix sum, then every lane takes whole slots, so lanes stay busy
+        // and each issues its two probes back to back.
+        uint32_t cnt = 0;
+        const uint4 *c0 = reinterpret_cast<const uint4 *>(w0);
+        for (uint32_t base = 0; base < words / 4; base += 32) {
+            const uint32_t q = base + lane;
+            const uint4 v = q < words / 4 ? __ldg(&c0[q]) : make_uint4(0, 0, 0, 0);
+            const uint32_t vw[4] = {v.x, v.y, v.z, v.w};
+            uint32_t n = 0;
+#pragma unroll
+            for (int j = 0; j < 16; j++) n += ((vw[j >> 2] >> (8 * (j & 3))) & CODE_MASK) ? 1u : 0u;
+            uint32_t incl = n;  // inclusive prefix sum over the warp
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t o = __shfl_up_sync(0xffffffffu, incl, d);
+                if (lane >= (uint32_t)d) incl += o;
+            }
+            const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+            uint32_t pos = incl - n;
+#pragma unroll
+            for (int j = 0; j < 16; j++) {
+                const uint32_t byte = (vw[j >> 2] >> (8 * (j & 3))) & 0xFFu;
+                if (byte & CODE_MASK) slots[pos++] = ((q * 16u + (uint32_t)j) << 8) | byte;
+            }
+            __syncwarp();
+            for (uint32_t e = lane; e < total; e += 32) {
+                const uint32_t ent = slots[e], h = ent >> 8, byte = ent & 0xFFu, code = byte & CODE_MASK;
+                const uint32_t t = (h >> s) & 3u;
+                const uint32_t pi = ((code - 1u) << s) | (h & r0m);
+                const uint32_t y1 = __ldg(&b1[slot4(t, pi, r1, s)]);
+                const uint32_t y2 = __ldg(&b2[slot4(t, pi, r2, s)]);
+                // smallest table missed by none of the three (each misses one, never t)
+                const uint32_t missed = (1u << (byte >> 6)) | (1u << (y1 >> 6)) | (1u << (y2 >> 6));
+                cnt += (y1 & CODE_MASK) == code && (y2 & CODE_MASK) == code &&
+                               (uint32_t)(__ffs(~missed) - 1) == t ? 1u : 0u;
+            }
+            __syncwarp();
+        }
+        cnt += failed_common<3, 4>(V, it, lane);
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, d);
+        if (lane == 0) sup[i] = cnt;
+    }
+}
+
 __global__ void k_unit_counts(const uint64_t *cand_off, uint64_t np, uint64_t *ucnt) {
     for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < np;
          p += (uint64_t)gridDim.x * blockDim.x)
@@ -642,13 +742,16 @@ __global__ void __launch_bounds__(WG_TPB) k_witness_group(View V, const uint32_t
         const uint32_t ma = ra / 4 - 1, mb = rb / 4 - 1;
         uint64_t cc[GROUP];
         uint32_t mc[GROUP], klim[GROUP], cnt[GROUP];
-        uint32_t kmax = 0;
+        uint32_t kmax = 0, probed = 0;  // probed: original slots routed to k_witness_probe
+        const uint32_t la = V.rlog[a], lb = V.rlog[b];
 #pragma unroll
         for (uint32_t j = 0; j < GROUP; j++) {
             cnt[j] = 0;
-            if (j < gn) {
-                const uint32_t c = cand[3 * (c0 + j) + 2];
-                const uint32_t rc = 1u << V.rlog[c];
+            const uint32_t c = j < gn ? cand[3 * (c0 + j) + 2] : 0u;
+            const uint32_t lc = j < gn ? V.rlog[c] : 0u;
+            if (j < gn && probe_route(la, lb, lc)) probed |= 1u << j;
+            if (j < gn && !((probed >> j) & 1u)) {
+                const uint32_t rc = 1u << lc;
                 cc[j] = V.base[c] >> 4;
                 mc[j] = rc / 4 - 1;
                 klim[j] = max(max(ra, rb), rc) / 16;  // chunks of one table this triple runs over
@@ -691,6 +794,7 @@ __global__ void __launch_bounds__(WG_TPB) k_witness_group(View V, const uint32_t
         for (uint32_t j = 0; j < GROUP; j++) {
             if (j >= gn) break;  // unused slots (klim = 0) sort last
             const uint32_t o = (pos >> (4 * j)) & 15u;
+            if ((probed >> o) & 1u) continue;  // written by k_witness_probe
             const uint32_t it[3] = {a, b, cand[3 * (c0 + o) + 2]};
             uint32_t v = cnt[j] + failed_common<3, 4>(V, it, lane);
 #pragma unroll
@@ -953,6 +1057,13 @@ void frequent_triples(batmap_set *S, uint32_t s, const uint32_t *d_pairs, uint64
             const uint64_t wpb = WG_TPB / 32;
             const unsigned grid = (unsigned)std::min<uint64_t>((n_units + wpb - 1) / wpb, 152ull * 64);
             k_witness_group<<<grid, WG_TPB, 0, st>>>(V, d_pairs, cnt.p, cand.p, units.p, n_units, sup.p);
+            BM_CHECK_LAUNCH();
+            DevBuf<uint32_t> plist(nc);
+            DevBuf<unsigned long long> pcount(1);
+            BM_CUDA(cudaMemsetAsync(pcount.p, 0, sizeof(unsigned long long), st));
+            k_route_probe<<<grid_for(nc), 256, 0, st>>>(cand.p, nc, S->d_rlog.p, plist.p, pcount.p);
+            BM_CHECK_LAUNCH();
+            k_witness_probe<<<152 * 16, 256, 0, st>>>(V, cand.p, plist.p, pcount.p, sup.p);
             BM_CHECK_LAUNCH();
         } else {
             launch_witness(V, S->d, 3, cand.p, nc, sup.p, st);  // one warp per candidate

@@ -164,6 +164,37 @@ def test_frequent_triples_exact(name, s):
     assert none[0] == 0 and none[2] == 0
 
 
+@pytest.mark.parametrize("params", [None, dict(load_num=1, load_den=1, max_loop=1)])
+def test_frequent_triples_probe_and_scan_routes_exact(params):
+    """Items of three densities (BatMap widths 2^15, 2^13 and 2^11 slots per
+    table at m = 20,000), so the candidates split between the scan (widths
+    within 8x) and the probe route (the widest at least 8x the narrowest);
+    s = 1 keeps every candidate, and every triple support is compared with
+    the merge oracle, also under forced failed insertions."""
+    import paper_1102_1003_gb300 as pkg
+    rng = np.random.default_rng(17)
+    m = 20_000
+    lists = [np.flatnonzero(rng.random(m) < p).astype(np.uint32) for p in [0.5] * 10 + [0.12] * 20 + [0.03] * 30]
+    inst = datagen.from_lists(lists, m, s=1)
+    pairs_ref, cand, want = _oracle_triples(inst, 1)
+    off, tids, _ = _dev(inst, 7)
+    p = pkg.batmap_default_params(perm_seed=7, **(params or {}))
+    b2 = pkg.batmap_build(inst.m, off, tids, None, params=p)
+    n_pairs, pairs = pkg.pair_support_all(b2, 1)
+    assert np.array_equal(pairs.cpu().numpy().astype(np.uint32), pairs_ref)
+    b3 = pkg.batmap_build_d(3, inst.m, off, tids, None, params=p)
+    # both routes occur: log2 of the widest over the narrowest table range, >= 3 probes
+    lg = np.log2(pkg.batmap_export_layout(b3)["range"].astype(np.float64)).astype(np.int64)
+    spread = lg[cand].max(axis=1) - lg[cand].min(axis=1)
+    assert (spread >= 3).sum() > 1000 and (spread < 3).sum() > 1000
+    if params:
+        assert b3.info["n_failed"] > 0
+    n_out, trip, n_cand = pkg.frequent_triples(b3, 1, pairs)
+    assert n_cand == cand.shape[0]
+    assert n_out == want.shape[0]
+    assert np.array_equal(trip.cpu().numpy().astype(np.uint32), want)
+
+
 def test_unsorted_pairs_rejected():
     import torch
     import paper_1102_1003_gb300 as pkg
