@@ -328,6 +328,8 @@ typedef struct batmap_timing {
     float compare_ms;   /* the persistent all-pairs compare launch              */
     float compact_ms;   /* failure correction + threshold compaction            */
     float pairs_ms;     /* whole pair_support_all                               */
+    float scan_ms;      /* frequent_triples: the witness scan kernel            */
+    float probe_ms;     /* frequent_triples: the probe kernel (width-skewed)    */
 } batmap_timing;
 
 /* Copy the phase durations of the set's most recent calls into *t. */

@@ -57,7 +57,8 @@ class batmap_info(ctypes.Structure):
 class batmap_timing(ctypes.Structure):
     _fields_ = [("build_ms", ctypes.c_float), ("place_ms", ctypes.c_float),
                 ("finalize_ms", ctypes.c_float), ("compare_ms", ctypes.c_float),
-                ("compact_ms", ctypes.c_float), ("pairs_ms", ctypes.c_float)]
+                ("compact_ms", ctypes.c_float), ("pairs_ms", ctypes.c_float),
+                ("scan_ms", ctypes.c_float), ("probe_ms", ctypes.c_float)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

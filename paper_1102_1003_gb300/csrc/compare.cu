@@ -625,13 +625,22 @@ struct Tile2 {
 
 // Tiles of the column class [cb, ce).  All pairs: the rows are every earlier
 // item, [0, c1 - 1).  Cross mode: the rows are the given range of the other
-// family (items no wider than the columns).
+// family (items no wider than the columns).  Tiles are listed in groups of
+// TILE_GROUP column strips, row strip by row strip inside a group, so the
+// tiles that run at the same time (consecutive in the queue) share row and
+// column strips and read them through L2 instead of each from DRAM.
+constexpr uint32_t TILE_GROUP = 12;
 static void class_tiles(uint32_t cb, uint32_t ce, const ShapeDesc &sh, std::vector<Tile2> *out,
                         bool cross = false, uint32_t row_lo = 0, uint32_t row_hi = 0) {
-    for (uint32_t c0 = cb; c0 < ce; c0 += sh.TC) {
-        uint32_t c1 = std::min(ce, c0 + sh.TC);
-        uint32_t lo = cross ? row_lo : 0, hi = cross ? row_hi : c1 - 1;
-        for (uint32_t r0 = lo; r0 < hi; r0 += sh.TR) out->push_back({r0, std::min(hi, r0 + sh.TR), c0, c1});
+    for (uint32_t g0 = cb; g0 < ce; g0 += TILE_GROUP * sh.TC) {
+        const uint32_t g1 = std::min(ce, g0 + TILE_GROUP * sh.TC);
+        const uint32_t lo = cross ? row_lo : 0, top = cross ? row_hi : g1 - 1;
+        for (uint32_t r0 = lo; r0 < top; r0 += sh.TR)
+            for (uint32_t c0 = g0; c0 < g1; c0 += sh.TC) {
+                const uint32_t c1 = std::min(ce, c0 + sh.TC);
+                const uint32_t hi = cross ? row_hi : c1 - 1;
+                if (r0 < hi) out->push_back({r0, std::min(hi, r0 + sh.TR), c0, c1});
+            }
     }
 }
 

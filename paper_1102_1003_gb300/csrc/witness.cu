@@ -1058,6 +1058,7 @@ void frequent_triples(batmap_set *S, uint32_t s, const uint32_t *d_pairs, uint64
             const unsigned grid = (unsigned)std::min<uint64_t>((n_units + wpb - 1) / wpb, 152ull * 64);
             k_witness_group<<<grid, WG_TPB, 0, st>>>(V, d_pairs, cnt.p, cand.p, units.p, n_units, sup.p);
             BM_CHECK_LAUNCH();
+            E.record(4, st);
             DevBuf<uint32_t> plist(nc);
             DevBuf<unsigned long long> pcount(1);
             BM_CUDA(cudaMemsetAsync(pcount.p, 0, sizeof(unsigned long long), st));
@@ -1088,6 +1089,9 @@ void frequent_triples(batmap_set *S, uint32_t s, const uint32_t *d_pairs, uint64
     S->timing.compare_ms = E.ms(1, 2);
     S->timing.compact_ms = E.ms(0, 1) + E.ms(2, 3);
     S->timing.pairs_ms = E.ms(0, 3);
+    const bool split = nc && grouped;  // event 4 sits between the scan and the probe kernels
+    S->timing.scan_ms = split ? E.ms(1, 4) : S->timing.compare_ms;
+    S->timing.probe_ms = split ? E.ms(4, 2) : 0.f;
     *n_out = total;
     if (total > cap)
         throw Error{BATMAP_ERR_CAPACITY, "d_out too small: " + std::to_string(total) + " triples qualify"};
