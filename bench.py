@@ -261,6 +261,8 @@ def dense_leg(args, inst, off, tids, n_out_ref, peaks, peak_kind, steps=None, wa
                          "traffic": _traffic(workload or args.workload, "k_dense_mmt", "dense.cu"),
                          "peak_kind": f"e4m3 dense = 2 x {peak_kind} bf16 burst (nominal 4.5/2.25 ratio)",
                          "algorithmic_flops": "2 m n(n-1)/2 (pairs i < j only)",
+                         "issued_definition": "two 128 x 256 tiles per upper-triangle block (diagonal "
+                                              "blocks included) over the padded K",
                          "issued_TFLOPs": flops_issued / g / 1e12,
                          "issued_frac": flops_issued / g / 1e12 / peak},
             "dtype": "e4m3 {0,1} operands, fp32 accumulate (exact integers < 2^24)"}
@@ -277,6 +279,16 @@ def _alu_peak(dev, peaks):
     return sms * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12, sms
 
 
+PROBE_LOG = 0  # batmap_params.probe_log of the timed builds (0 = the library's default)
+
+
+def _build_params():
+    """Build parameters of the timed BatMap builds: the defaults, with
+    probe_log from --probe-log."""
+    import paper_1102_1003_gb300 as pkg
+    return pkg.batmap_default_params(probe_log=PROBE_LOG)
+
+
 def plain_leg(inst, dev, steps, warmup, peaks, peak_kind, workload, sampler=None, dist=None):
     """Time `steps` plain steps (batmap_build + pair_support_all) on resident tidlists."""
     import torch
@@ -286,20 +298,22 @@ def plain_leg(inst, dev, steps, warmup, peaks, peak_kind, workload, sampler=None
     off = torch.from_numpy(inst.offsets.astype(np.int64)).to(dev)
     tids = torch.from_numpy(inst.tids.view(np.int32)).to(dev)
     npairs = inst.n * (inst.n - 1) // 2
-    bset = pkg.batmap_build(inst.m, off, tids, None)
+    bset = pkg.batmap_build(inst.m, off, tids, None, params=_build_params())
     n_out, _ = pkg.pair_support_all(bset, inst.s)
     info = bset.info
     bset.free()
     pairs_buf = torch.empty((max(n_out, 1), 3), dtype=torch.int32, device=dev)
     timing = B.batmap_timing()
-    compare_ms, build_ms, compact_ms = [], [], []
+    compare_ms, build_ms, compact_ms, scan_ms, probe_ms = [], [], [], [], []
 
     def step(record):
-        bs = pkg.batmap_build(inst.m, off, tids, None)
+        bs = pkg.batmap_build(inst.m, off, tids, None, params=_build_params())
         k, _ = pkg.pair_support_all(bs, inst.s, pairs=pairs_buf)
         if record:
             L.batmap_get_timing(bs.handle, ctypes.byref(timing))
             compare_ms.append(timing.compare_ms)
+            scan_ms.append(timing.scan_ms)
+            probe_ms.append(timing.probe_ms)
             build_ms.append(timing.build_ms)
             compact_ms.append(timing.compact_ms)
         bs.free()
@@ -328,9 +342,12 @@ def plain_leg(inst, dev, steps, warmup, peaks, peak_kind, workload, sampler=None
     clocks = sampler.stop() if sampler else None
     assert got == n_out
     cmp_s = statistics.mean(compare_ms) / 1e3
+    scan_s = statistics.mean(scan_ms) / 1e3
     wp = info["word_pairs"]
+    wp_probe = info["probe_word_pairs"]
+    wp_scan = wp - wp_probe
     alu_peak, sms = _alu_peak(dev, peaks)
-    achieved = OPS_PER_WORD_PAIR * wp / cmp_s / 1e12
+    achieved = OPS_PER_WORD_PAIR * wp_scan / scan_s / 1e12
     logical_gbs = 8.0 * wp / cmp_s / 1e9
     rec = {
         "value": npairs * steps / elapsed, "unit": UNIT, "steps": steps, "warmup": warmup,
@@ -343,16 +360,31 @@ def plain_leg(inst, dev, steps, warmup, peaks, peak_kind, workload, sampler=None
                      "traffic": _traffic(workload),
                      "peak_kind": f"{sms} SMs x 128 INT32 lanes x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz "
                                   f"({peak_kind} max clock)",
-                     "algorithmic_ops": f"{OPS_PER_WORD_PAIR} x {wp:.4g} word pairs"},
+                     "algorithmic_ops": f"{OPS_PER_WORD_PAIR} x {wp_scan:.4g} word pairs (the scan-routed pairs' "
+                                        f"max(|B_i|,|B_j|)/4) per scan time {1e3 * scan_s:.3f} ms"},
         "logical_hbm": {"achieved_GBps": logical_gbs, "peak_GBps": peaks["hbm_gbs"],
                         "frac": logical_gbs / peaks["hbm_gbs"],
                         "definition": "sum over pairs of 2*max(|B_i|,|B_j|) bytes / compare time (Sec. IV-A)"},
         "set_elements_per_s": (inst.n - 1) * int(inst.tids.size) / cmp_s,
         "phases_ms": {"build": statistics.mean(build_ms), "compare": statistics.mean(compare_ms),
+                      "compare_scan": statistics.mean(scan_ms), "compare_probe": statistics.mean(probe_ms),
                       "correct_compact": statistics.mean(compact_ms)},
         "frequent_pairs": n_out, "failed_insertions": info["n_failed"], "gpu_launches": int(launches),
         "clocks": clocks,
     }
+    if wp_probe > 0:
+        probe_s = statistics.mean(probe_ms) / 1e3
+        rec["probe"] = {
+            "kernel": "k_pair_probe", "ms": 1e3 * probe_s, "routed_word_pairs": wp_probe,
+            "routed_share": wp_probe / wp, "words_read": info["probe_words"],
+            "scan_equivalent_frac": OPS_PER_WORD_PAIR * wp_probe / probe_s / 1e12 / alu_peak,
+            "definition": "pairs whose BatMap widths differ by 2^probe_log or more (default 32x) are counted "
+                          "by probing the narrower BatMap's nonempty slots; routed_word_pairs is the scan's "
+                          "work for them (max(|B_i|,|B_j|)/4 per pair), words_read the probe's "
+                          "(min(|B_i|,|B_j|)/4 per pair); scan_equivalent_frac = 4 x routed_word_pairs / "
+                          "probe time / lane-op peak",
+            "traffic": _traffic(workload, "k_pair_probe"),
+        }
     return rec, off, tids, n_out
 
 
@@ -408,6 +440,8 @@ def run_mine(args, inst, rank, world):
                 "d2h_bytes_per_step": int(12 * n_out + 8)},
         "clocks": rec["clocks"],
     }
+    if "probe" in rec:
+        line["probe"] = rec["probe"]
     if not args.no_dense and inst.m <= (1 << 24):
         line["dense"] = dense_leg(args, inst, off, tids, n_out, peaks, peak_kind, workload=label)
     del off, tids
@@ -463,7 +497,7 @@ def batch_record(args, steps, warmup, small=False, instances=64, autotune=True):
     for inst in insts:
         off = torch.from_numpy(inst.offsets.view(np.int64)).to(dev)
         tids = torch.from_numpy(inst.tids.view(np.int32)).to(dev)
-        sets.append(pkg.batmap_build(inst.m, off, tids, None))
+        sets.append(pkg.batmap_build(inst.m, off, tids, None, params=_build_params()))
         npairs += inst.n * (inst.n - 1) // 2
         del off, tids
     torch.cuda.synchronize()
@@ -508,7 +542,11 @@ def batch_record(args, steps, warmup, small=False, instances=64, autotune=True):
     for name, c in (("plain", cmp_plain), ("batched", cmp_batch)):
         t = statistics.mean(c) / 1e3
         results[name]["compare_ms"] = 1e3 * t
-        results[name]["compare_lane_op_frac"] = OPS_PER_WORD_PAIR * wp / t / 1e12 / alu_peak
+        results[name]["compare_equiv_lane_op_frac"] = OPS_PER_WORD_PAIR * wp / t / 1e12 / alu_peak
+    results["compare_equiv_definition"] = (
+        "4 x sum over all pairs of max(|B_i|,|B_j|)/4 word pairs (the scan's work for every pair, "
+        "probe-routed pairs included) / compare time / lane-op peak")
+    results["probe_routed_share"] = sum(b.info["probe_word_pairs"] for b in sets) / wp
     # batched and plain give identical outputs; a sampled oracle check per instance
     batch_pairs = [b[:k].cpu().numpy().copy() for b, k in zip(bufs, n_out)]
     plain(False)
@@ -531,6 +569,8 @@ def batch_record(args, steps, warmup, small=False, instances=64, autotune=True):
     return {"workload": "batch", "unit": UNIT, "value": results["batched"]["value"],
             "ms_per_step": results["batched"]["ms_per_step"], "steps": steps, "warmup": warmup,
             "batched": results["batched"], "plain": results["plain"],
+            "compare_equiv_definition": results["compare_equiv_definition"],
+            "probe_routed_share": results["probe_routed_share"],
             "speedup_batched_over_plain": results["batched"]["value"] / results["plain"]["value"],
             "config": {"instances": len(insts), "small": bool(small), "pairs": npairs,
                        "tids": int(sum(i.tids.size for i in insts)), "word_pairs": wp,
@@ -615,14 +655,14 @@ def run_cross(args):
     tids = torch.from_numpy(union.tids.view(np.int32)).to(dev)
     perm = torch.from_numpy(datagen.permutations(union.m, 5).view(np.int32)).to(dev)
     full = torch.empty(npairs, dtype=torch.int32, device=dev)
-    b = pkg.batmap_build_cross(union.m, na, off, tids, perm)
+    b = pkg.batmap_build_cross(union.m, na, off, tids, perm, params=_build_params())
     n_out, _ = pkg.pair_support_all(b, 1)
     info = b.info
     b.free()
     pairs = torch.empty((max(n_out, 1), 3), dtype=torch.int32, device=dev)
 
     def step():
-        bs = pkg.batmap_build_cross(union.m, na, off, tids, perm)
+        bs = pkg.batmap_build_cross(union.m, na, off, tids, perm, params=_build_params())
         k, _ = pkg.pair_support_all(bs, 1, pairs=pairs, full=full)
         t = pkg.batmap_get_timing(bs)
         bs.free()
@@ -654,11 +694,11 @@ def run_cross(args):
     ref = oracle.pairs_list(union.offsets, union.tids, ia, na + jb, threads=os.cpu_count() or 4)
     got = full.cpu().numpy().astype(np.uint32)[ia * nb + jb]
     peaks, peak_kind = _peaks()
-    cmp_s = statistics.mean(t["compare_ms"] for t in phases) / 1e3
-    wp = info["word_pairs"]
+    scan_s = statistics.mean(t["scan_ms"] for t in phases) / 1e3
+    wp_scan = info["word_pairs"] - info["probe_word_pairs"]
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     alu_peak = sms * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-    achieved = OPS_PER_WORD_PAIR * wp / cmp_s / 1e12
+    achieved = OPS_PER_WORD_PAIR * wp_scan / scan_s / 1e12
     line = {"metric": "A x B pair supports/sec (sparse boolean matrix multiplication), bit-exact",
             "workload": "cross", "unit": UNIT, "value": npairs * args.steps / elapsed, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
@@ -671,8 +711,11 @@ def run_cross(args):
                          "frac": achieved / alu_peak, "kernel": "k_compare", "traffic": None,
                          "peak_kind": f"{sms} SMs x 128 INT32 lanes x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz "
                                       f"({peak_kind} max clock)",
-                         "algorithmic_ops": f"{OPS_PER_WORD_PAIR} x {wp:.4g} word pairs"},
-            "phases_ms": {p: statistics.mean(t[p] for t in phases) for p in ("build_ms", "compare_ms", "compact_ms")},
+                         "algorithmic_ops": f"{OPS_PER_WORD_PAIR} x {wp_scan:.4g} word pairs (the scan-routed pairs' "
+                                        f"max(|B_i|,|B_j|)/4) per scan time {1e3 * scan_s:.3f} ms"},
+            "phases_ms": {p: statistics.mean(t[p] for t in phases)
+                          for p in ("build_ms", "compare_ms", "scan_ms", "probe_ms", "compact_ms")},
+            "probe_routed_share": info["probe_word_pairs"] / max(info["word_pairs"], 1.0),
             "nonempty_pairs": n_out, "failed_insertions": info["n_failed"], "gpu_launches": int(launches),
             "parity_sample": {"pairs": int(ia.size), "exact": bool(np.array_equal(got, ref))},
             "clocks": clocks}
@@ -911,6 +954,9 @@ def main():
     ap.add_argument("--batch-small", action="store_true",
                     help="batch workload of small instances (m in [1e3, 1e5], n in [50, 400])")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--probe-log", type=int, default=0,
+                    help="batmap_params.probe_log: pairs whose widths differ by 2^k or more are probed "
+                         "(0 = library default, 32 = scan every pair)")
     ap.add_argument("--pool-sets", type=int, default=100_000, help="serving pool size (serve workload)")
     ap.add_argument("--queries", type=int, default=200_000, help="queries per serving run (serve workload)")
     ap.add_argument("--max-batch", type=int, default=256)
@@ -923,6 +969,8 @@ def main():
     ap.add_argument("--no-sub", action="store_true",
                     help="skip the sub-records (Zipf workload, batched vs plain) of the default line")
     args = ap.parse_args()
+    global PROBE_LOG
+    PROBE_LOG = args.probe_log
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.workload in ("serve", "batch", "nsweep", "cross", "triples"):

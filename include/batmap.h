@@ -64,13 +64,26 @@ typedef int batmap_status;
  *       Must be >= 7 so that every BatMap is a multiple of 384 bytes.
  *       Default 7.
  *   tile : 0 lets the scheduler choose compare tile shapes per width class;
- *       1..16 forces one shape for every class (testing and autotuning).
+ *       1..BATMAP_NUM_SHAPES forces one shape for every class (testing and
+ *       autotuning).
  *   validate : nonzero checks that tids are strictly increasing and < m per
  *       item and that each permutation row is a bijection of [0, m); a
  *       violation returns BATMAP_ERR_ARG.  Default 1.
- *   shape_mask : bit s-1 allows compare tile shape s (1..16) when tile is 0;
+ *   shape_mask : bit s-1 allows compare tile shape s (1..BATMAP_NUM_SHAPES)
+ *       when tile is 0;
  *       0 allows every shape.  Default 0.
- *   reserved : must be 0.
+ *   probe_log : width-skewed pairs may be counted by probing instead of the
+ *       cyclic scan (Sec. V's second k-way idea: look up the elements of the
+ *       smaller set in the larger one).  A pair whose wider BatMap is at least
+ *       2^probe_log times as wide as the narrower is eligible; the probe
+ *       visits every nonempty slot of the narrower BatMap and reads the one
+ *       slot of the wider BatMap that can hold the same element: a slot in
+ *       table t at byte h with code c holds pi_t(x) = ((c - 1) << s) |
+ *       (h mod r_0).  Per width class the scheduler probes the eligible rows
+ *       where its cost model (the measured rates of both routes) makes the
+ *       probe cheaper.  Both routes count the same slot pairs, so supports
+ *       are identical.  0 selects the default, 2 (ratio 4); 32 or more turns
+ *       the route off.  Ignored when `tile` forces a shape.  Default 0.
  *   perm_seed : seed of the permutations pi_t that the library computes when
  *       a build is given no permutation table (d_perm = NULL).  Sec. III-A
  *       draws pi_1..pi_3 at random without fixing a generator; the library's
@@ -85,6 +98,9 @@ typedef int batmap_status;
  *       value is below m (cycle walking).  Computed in the kernels; no table
  *       is stored.  Default 1.
  */
+/* Number of compare tile shapes (batmap_params.tile, shape_mask, autotune). */
+#define BATMAP_NUM_SHAPES 18
+
 typedef struct batmap_params {
     uint32_t load_num;
     uint32_t load_den;
@@ -93,7 +109,7 @@ typedef struct batmap_params {
     uint32_t tile;
     uint32_t validate;
     uint32_t shape_mask;
-    uint32_t reserved;
+    uint32_t probe_log;
     uint64_t perm_seed;
 } batmap_params;
 
@@ -116,6 +132,9 @@ typedef struct batmap_info {
     double word_pairs;       /* sum over reported pairs of max(|B_i|,|B_j|)/4  */
     uint32_t d;              /* copies per element: 2 (2-of-3) or 3 (3-of-4)   */
     uint32_t reserved;
+    double probe_word_pairs; /* part of word_pairs counted by the probe route  */
+    double probe_words;      /* words the probe route reads: sum over probe-
+                                routed pairs of min(|B_i|,|B_j|)/4             */
 } batmap_info;
 
 /* Fills *p with the defaults documented above. */
@@ -271,7 +290,10 @@ batmap_status batmap_export_layout(const batmap_set *set, uint8_t *h_bytes,
 
 /*
  * Support of every item pair and the frequent pairs (Sec. I problem
- * statement; Sec. III-B/C all-pairs comparison, failure correction).
+ * statement; Sec. III-B/C all-pairs comparison, failure correction).  Pairs
+ * of similar width run the cyclic scan; pairs whose widths differ by
+ * 2^probe_log or more run the probe route (batmap_params.probe_log); both
+ * count the same slot pairs.
  *   s       : support threshold; pairs with support >= s are reported.
  *   d_pairs : device uint32[3*cap]: triples (i, j, support) with original
  *             item ids i < j, in lexicographic (i, j) order.  May be NULL
@@ -311,7 +333,8 @@ batmap_status pair_support_host(const batmap_params *p, uint32_t m, uint32_t n,
  * batmap_build in the process, and all k sets are rescheduled with them (the
  * width class -> tile shape choice and the split of column words into work
  * units).
- *   shape_eff : optional host double[16], receives the relative throughputs.
+ *   shape_eff : optional host double[BATMAP_NUM_SHAPES], receives the
+ *               relative throughputs.
  * Synchronises the stream.
  */
 batmap_status batmap_autotune(batmap_set *const *sets, uint32_t k, double *shape_eff, cudaStream_t stream);
@@ -325,11 +348,13 @@ typedef struct batmap_timing {
     float build_ms;     /* whole batmap_build, first to last enqueued operation */
     float place_ms;     /* 2-of-3 placement kernel                              */
     float finalize_ms;  /* byte writing + failure lists + correction entries    */
-    float compare_ms;   /* the persistent all-pairs compare launch              */
+    float compare_ms;   /* the all-pairs compare: scan and probe kernels        */
     float compact_ms;   /* failure correction + threshold compaction            */
     float pairs_ms;     /* whole pair_support_all                               */
-    float scan_ms;      /* frequent_triples: the witness scan kernel            */
-    float probe_ms;     /* frequent_triples: the probe kernel (width-skewed)    */
+    float scan_ms;      /* frequent_triples: the witness scan kernel;
+                           pair_support_all: the cyclic-scan compare kernels    */
+    float probe_ms;     /* frequent_triples and pair_support_all: the probe
+                           kernel of width-skewed tuples                        */
 } batmap_timing;
 
 /* Copy the phase durations of the set's most recent calls into *t. */

@@ -7,7 +7,7 @@ library; there is no CPU fallback.
 """
 from .batmap import (  # noqa: F401
     BATMAP_ERR_ARG, BATMAP_ERR_CAPACITY, BATMAP_ERR_CUDA, BATMAP_ERR_INTERNAL, BATMAP_ERR_NOMEM,
-    BATMAP_ERR_TIMEOUT, BATMAP_OK, BatmapError, BatMapSet, batmap_build, batmap_default_params,
+    BATMAP_ERR_TIMEOUT, BATMAP_OK, NUM_SHAPES, BatmapError, BatMapSet, batmap_build, batmap_default_params,
     batmap_export_layout, batmap_free, batmap_get_info, batmap_get_timing, batmap_kernel_launches,
     load_library, pair_support_all,
     pair_support_batch, pair_support_dense, pair_support_host, pair_threshold_noalloc,

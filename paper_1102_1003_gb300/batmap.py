@@ -22,6 +22,7 @@ BATMAP_ERR_CAPACITY = -3
 BATMAP_ERR_CUDA = -4
 BATMAP_ERR_TIMEOUT = -5
 BATMAP_ERR_INTERNAL = -6
+NUM_SHAPES = 18  # BATMAP_NUM_SHAPES: compare tile shapes
 
 EXPORTED = [
     "batmap_default_params", "batmap_last_error", "batmap_build", "batmap_free",
@@ -38,7 +39,7 @@ class batmap_params(ctypes.Structure):
     _fields_ = [("load_num", ctypes.c_uint32), ("load_den", ctypes.c_uint32),
                 ("max_loop", ctypes.c_uint32), ("min_shift", ctypes.c_uint32),
                 ("tile", ctypes.c_uint32), ("validate", ctypes.c_uint32),
-                ("shape_mask", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("shape_mask", ctypes.c_uint32), ("probe_log", ctypes.c_uint32),
                 ("perm_seed", ctypes.c_uint64)]
 
 
@@ -48,7 +49,8 @@ class batmap_info(ctypes.Structure):
                 ("n_elements", ctypes.c_uint64), ("n_failed", ctypes.c_uint64),
                 ("n_corrections", ctypes.c_uint64), ("n_work_units", ctypes.c_uint64),
                 ("n_classes", ctypes.c_uint32), ("n_a", ctypes.c_uint32),
-                ("word_pairs", ctypes.c_double), ("d", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("word_pairs", ctypes.c_double), ("d", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("probe_word_pairs", ctypes.c_double), ("probe_words", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -461,11 +463,11 @@ def batmap_test_dense_timeout(spin_limit: int):
 
 def batmap_autotune(sets, stream=None):
     """Measure every tile shape on these sets, adopt the result for scheduling and
-    reschedule them; returns the relative throughput per shape (1..16)."""
+    reschedule them; returns the relative throughput per shape (1..NUM_SHAPES)."""
     L = load_library()
     k = len(sets)
     handles = (ctypes.c_void_p * k)(*[b.handle for b in sets])
-    eff = (ctypes.c_double * 16)()
+    eff = (ctypes.c_double * NUM_SHAPES)()
     _check(L.batmap_autotune(handles, k, eff, _stream_handle(stream)))
     return list(eff)
 

@@ -26,7 +26,7 @@ struct BatchPlan {
     DevBuf<WorkUnit> d_units;
     DevBuf<uint32_t> d_counter;
     DevBuf<uint64_t> d_totals;
-    uint32_t nunits = 0, nmain = 0;
+    UnitParts parts;
     cudaStream_t stream = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -62,10 +62,10 @@ static void enqueue_batch(BatchPlan *P, batmap_set *const *sets, const uint32_t 
         const uint64_t np = sets[q]->npairs();
         if (np) BM_CUDA(cudaMemsetAsync(P->C[q], 0, np * sizeof(uint32_t), st));
     }
-    BM_CUDA(cudaMemsetAsync(P->d_counter.p, 0, 2 * sizeof(uint32_t), st));
+    BM_CUDA(cudaMemsetAsync(P->d_counter.p, 0, COMPARE_COUNTERS * sizeof(uint32_t), st));
     BM_CUDA(cudaMemsetAsync(P->d_stamps.p, 0xFF, sizeof(unsigned long long), st));
     BM_CUDA(cudaMemsetAsync(P->d_stamps.p + 1, 0, sizeof(unsigned long long), st));
-    launch_compare(P->d_views.p, P->d_units.p, P->nunits, P->nmain, P->d_counter.p, st, P->d_stamps.p);
+    launch_compare(P->d_views.p, P->d_units.p, P->parts, P->d_counter.p, st, P->d_stamps.p);
     for (uint32_t q = 0; q < k; q++)
         enqueue_correct_compact(sets[q], P->C[q], s[q], outs[q].d_pairs, outs[q].cap, P->d_totals.p + q, st);
 }
@@ -87,7 +87,7 @@ static BatchPlan *make_plan(batmap_set *const *sets, const uint32_t *s, uint32_t
         }
         P->C[q] = C;
         views[q] = InstView{reinterpret_cast<const uint4 *>(S->d_bm.p), S->d_line_off.p, S->d_wshift.p,
-                            S->d_order.p, C, S->n, S->n_a};
+                            S->d_order.p, C, S->n, S->n_a, S->shift};
         for (WorkUnit u : S->units) {
             u.inst = q;
             units.push_back(u);
@@ -95,11 +95,10 @@ static BatchPlan *make_plan(batmap_set *const *sets, const uint32_t *s, uint32_t
         prepare_compaction(S);
     }
     sort_units(&units);
-    P->nunits = (uint32_t)units.size();
-    P->nmain = main_units(units);
+    P->parts = unit_parts(units);
     P->d_views.alloc(k);
     P->d_units.alloc(units.size());
-    P->d_counter.alloc(2);
+    P->d_counter.alloc(COMPARE_COUNTERS);
     P->d_totals.alloc(k);
     P->d_stamps.alloc(2);
     BM_CUDA(cudaMemcpyAsync(P->d_views.p, views.data(), k * sizeof(InstView), cudaMemcpyHostToDevice, st));
@@ -210,10 +209,10 @@ void autotune(batmap_set *const *sets, uint32_t k, double *eff_out, cudaStream_t
         batmap_set *S = sets[q];
         S->d_C.ensure(S->npairs());
         views.push_back(InstView{reinterpret_cast<const uint4 *>(S->d_bm.p), S->d_line_off.p, S->d_wshift.p,
-                                 S->d_order.p, S->d_C.p, S->n, S->n_a});
+                                 S->d_order.p, S->d_C.p, S->n, S->n_a, S->shift});
     }
     DevBuf<InstView> d_views(views.size());
-    DevBuf<uint32_t> d_counter(2);
+    DevBuf<uint32_t> d_counter(COMPARE_COUNTERS);
     BM_CUDA(cudaMemcpyAsync(d_views.p, views.data(), views.size() * sizeof(InstView), cudaMemcpyHostToDevice, st));
     PhaseEvents ev;
     ev.create();
@@ -236,9 +235,9 @@ void autotune(batmap_set *const *sets, uint32_t k, double *eff_out, cudaStream_t
         DevBuf<WorkUnit> d_units(units.size());
         if (!units.empty())
             BM_CUDA(cudaMemcpyAsync(d_units.p, units.data(), units.size() * sizeof(WorkUnit), cudaMemcpyHostToDevice, st));
-        BM_CUDA(cudaMemsetAsync(d_counter.p, 0, 2 * sizeof(uint32_t), st));
+        BM_CUDA(cudaMemsetAsync(d_counter.p, 0, COMPARE_COUNTERS * sizeof(uint32_t), st));
         ev.record(0, st);
-        launch_compare(d_views.p, d_units.p, (uint32_t)units.size(), main_units(units), d_counter.p, st);
+        launch_compare(d_views.p, d_units.p, unit_parts(units), d_counter.p, st);
         ev.record(1, st);
         BM_CUDA(cudaStreamSynchronize(st));
         const double ms = ev.ms(0, 1);

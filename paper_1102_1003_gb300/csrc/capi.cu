@@ -55,11 +55,10 @@ static batmap_status guarded(F &&f) {
 void enqueue_compare(batmap_set *S, uint32_t *C, const InstView *d_view, cudaStream_t st) {
     const uint64_t npairs = S->npairs();
     if (npairs) BM_CUDA(cudaMemsetAsync(C, 0, npairs * sizeof(uint32_t), st));
-    S->d_counters.ensure(2);
-    BM_CUDA(cudaMemsetAsync(S->d_counters.p, 0, 2 * sizeof(uint32_t), st));
-    const uint32_t count = (uint32_t)S->units.size();
+    S->d_counters.ensure(COMPARE_COUNTERS);
+    BM_CUDA(cudaMemsetAsync(S->d_counters.p, 0, COMPARE_COUNTERS * sizeof(uint32_t), st));
     S->pairs_ev.record(1, st);
-    launch_compare(d_view, S->d_units.p, count, main_units(S->units), S->d_counters.p, st);
+    launch_compare(d_view, S->d_units.p, unit_parts(S->units), S->d_counters.p, st, nullptr, S->pairs_ev.ev[4]);
     S->pairs_ev.record(2, st);
 }
 
@@ -78,7 +77,7 @@ void batmap_default_params(batmap_params *p) {
     p->tile = 0;
     p->validate = 1;
     p->shape_mask = 0;
-    p->reserved = 0;
+    p->probe_log = 0;
     p->perm_seed = 1;
 }
 
@@ -97,7 +96,7 @@ static batmap_status build_any(const batmap_params *p, uint32_t m, uint32_t n, u
         BM_REQUIRE(P.load_num >= 1 && P.load_den >= 1 && P.load_num <= 16 * P.load_den,
                    BATMAP_ERR_ARG, "load factor must be in [1/load_den, 16]");
         BM_REQUIRE(P.min_shift >= 7 && P.min_shift <= 24, BATMAP_ERR_ARG, "min_shift must be in [7, 24]");
-        BM_REQUIRE(P.tile <= NUM_SHAPES, BATMAP_ERR_ARG, "tile must be 0..16");
+        BM_REQUIRE(P.tile <= NUM_SHAPES, BATMAP_ERR_ARG, "tile must be 0..BATMAP_NUM_SHAPES (18)");
         BM_REQUIRE(P.max_loop >= 1 && P.max_loop <= (1u << 20), BATMAP_ERR_ARG, "max_loop out of range");
         batmap_set *S = new batmap_set();
         S->params = P;
@@ -189,6 +188,8 @@ batmap_status batmap_get_info(const batmap_set *S, batmap_info *info) {
         info->n_classes = S->class_begin.empty() ? 0 : (uint32_t)S->class_begin.size() - 1;
         info->n_a = S->n_a;
         info->word_pairs = S->word_pairs;
+        info->probe_word_pairs = S->probe_word_pairs;
+        info->probe_words = S->probe_words;
         info->d = S->d;
     });
 }
@@ -228,7 +229,7 @@ static void pair_support_impl(batmap_set *S, uint32_t s, uint32_t *d_pairs, uint
     }
     static thread_local InstView h_view;
     h_view = InstView{reinterpret_cast<const uint4 *>(S->d_bm.p), S->d_line_off.p, S->d_wshift.p,
-                      S->d_order.p, C, S->n, S->n_a};
+                      S->d_order.p, C, S->n, S->n_a, S->shift};
     S->d_total.ensure(1);
     S->d_view.ensure(1);
     S->pairs_ev.create();
@@ -241,6 +242,8 @@ static void pair_support_impl(batmap_set *S, uint32_t s, uint32_t *d_pairs, uint
     BM_CUDA(cudaMemcpyAsync(&total, S->d_total.p, 8, cudaMemcpyDeviceToHost, st));
     BM_CUDA(cudaStreamSynchronize(st));
     S->timing.compare_ms = S->pairs_ev.ms(1, 2);
+    S->timing.scan_ms = S->pairs_ev.ms(1, 4);
+    S->timing.probe_ms = S->pairs_ev.ms(4, 2);
     S->timing.compact_ms = S->pairs_ev.ms(2, 3);
     S->timing.pairs_ms = S->pairs_ev.ms(0, 3);
     *n_out = total;

@@ -167,6 +167,7 @@ struct InstView {
     uint32_t *C;              // supports: packed upper triangle (original ids), or n_a x (n - n_a) in cross mode
     uint32_t n;
     uint32_t n_a;             // 0: all pairs i < j; else cross pairs of items [0, n_a) with [n_a, n)
+    uint32_t shift;           // s: r_0 = 2^s, codes (pi >> s) + 1 (the probe route decodes slots)
 };
 
 // Index of the support of the pair of original items (oi, oj) in C.
@@ -187,6 +188,8 @@ struct batmap_set {
     uint64_t npairs() const { return n_a ? (uint64_t)n_a * (n - n_a) : (uint64_t)n * (n > 0 ? n - 1 : 0) / 2; }
     uint64_t n_elements = 0, bytes = 0, n_failed = 0, n_corr = 0;
     double word_pairs = 0.0;
+    double probe_word_pairs = 0.0;  // part of word_pairs counted by the probe route (scan-equivalent words)
+    double probe_words = 0.0;       // words the probe route reads: rows' widths x columns per unit
     uint32_t n_a = 0;            // cross mode: items [0, n_a) x [n_a, n); 0 = all pairs
     uint32_t d = 2;              // copies per element: 2 (2-of-3 BatMaps) or 3 (3-of-4, k-way witnesses)
     uint64_t gen = 0;            // unique build id (batch plans key on it)

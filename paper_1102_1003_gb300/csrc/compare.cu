@@ -50,6 +50,11 @@ const ShapeDesc SHAPES[NUM_SHAPES] = {
     // (priors from batmap_autotune on 1,024 instances with m in [1e3, 1e5], n in [50, 400])
     {14, 256, 8, 1, 32, 3, 0.545},   {15, 128, 16, 1, 32, 3, 0.599},
     {16, 64, 32, 1, 32, 3, 0.619},
+    // 12 column-staged columns over 256 or 512 rows (1 or 2 rows per thread):
+    // the near-width rows that the probe route leaves to the scan in classes
+    // of few wide items (priors from unit timings on the m = 10^6, n = 2,000
+    // Zipf workload)
+    {17, 256, 12, 12, 4, 0, 0.65},   {18, 512, 12, 12, 4, 0, 0.80},
 };
 
 int device_sms() {
@@ -479,6 +484,12 @@ __device__ __forceinline__ void process_unit_direct(uint4 *smem, const InstView 
     X(14, 16, 16, 1, 32, 3)       \
     X(15, 8, 32, 1, 32, 3)
 
+// Column-staged streaming shapes with few rows per thread (shapes 17, 18),
+// run by the small-shape kernel.
+#define BM_DIRECT_SMALL_LIST(X)  \
+    X(16, 256, 1, 12, 1, true)   \
+    X(17, 256, 1, 12, 2, true)
+
 #define BM_DIRECT_LIST(X)      \
     X(6, 16, 16, 8, 8, false)    \
     X(7, 32, 8, 8, 8, false)     \
@@ -550,9 +561,10 @@ k_compare(const InstView *__restrict__ views, const WorkUnit *__restrict__ units
     stamp_end(stamps);
 }
 
-// The one-column-per-thread shapes run in a kernel of their own (after the
-// main one, on its own counter), so that they leave the register allocation
-// of the main shapes' loops untouched.
+// The one-column-per-thread shapes 14..16 and the few-rows streaming shapes
+// 17, 18 run in a kernel of their own (after the main one, on its own
+// counter), so that they leave the register allocation of the main shapes'
+// loops untouched.
 __global__ void __launch_bounds__(256, 1)
 k_compare_small(const InstView *__restrict__ views, const WorkUnit *__restrict__ units, uint32_t count,
                 uint32_t *__restrict__ counter, unsigned long long *stamps) {
@@ -571,10 +583,118 @@ k_compare_small(const InstView *__restrict__ views, const WorkUnit *__restrict__
 #define X(i, a, b, c, d, e) case i: process_unit<a, b, c, d, e>(smem, V, wu); break;
             BM_SMALL_LIST(X)
 #undef X
+#define X(i, a, b, c, d, e) case i: process_unit_direct<a, b, c, d, e>(smem, V, wu); break;
+            BM_DIRECT_SMALL_LIST(X)
+#undef X
             default: break;
         }
     }
     stamp_end(stamps);
+}
+
+// ---- probe route for width-skewed pairs (Sec. V: look up the smaller set) ----
+//
+// A nonempty slot of row item i in table t at byte h holds a copy of some x
+// with pi_t(x) = ((code - 1) << s) | (h mod r_0): the code carries the bits
+// above s and the slot the bits below (r_0 = 2^s divides every range).  The
+// cyclic scan pairs that slot with the r_j / r_i slots of column item j that
+// share its table and its position modulo r_i; of those, only the slot of
+// pi_t(x) in j, 3 r_0 floor((pi_t(x) mod r_j) / r_0) + t r_0 + (h mod r_0),
+// can carry the same code (equal code and equal low bits mean equal pi_t,
+// and pi_t is a bijection).  Reading that one byte and applying the counting
+// rule (equal element bits, an indicator set) therefore adds the same count
+// as the scan, r_j / r_i times fewer comparisons, at the price of one random
+// byte read per nonempty row slot and column.
+
+// One warp: every row of the unit against its (at most PROBE_COLS) columns.
+// Lanes read 16-byte chunks of the row, pack the nonempty slots (slot index
+// within the 32 chunks << 8 | byte) into shared memory by a warp prefix
+// sum, then take whole slots, each decoded once and probed in every column.
+__device__ __forceinline__ void probe_unit(const InstView &V, const WorkUnit &wu, uint32_t *ent, uint32_t lane) {
+    const uint32_t s = V.shift, r0m = (1u << s) - 1u;
+    const uint32_t nc = wu.c1 - wu.c0;
+    const uint32_t rcm = (4u << __ldg(&V.wshift[wu.c0])) - 1u;  // r_j - 1 for the column class
+    const uint8_t *bytes = reinterpret_cast<const uint8_t *>(V.bm);
+    const uint8_t *col[PROBE_COLS];
+#pragma unroll
+    for (uint32_t b = 0; b < PROBE_COLS; b++)
+        col[b] = bytes + (size_t)__ldg(&V.line_off[wu.c0 + (b < nc ? b : 0)]) * 128u;
+    const uint64_t n = V.n;
+    for (uint32_t q = wu.r0; q < wu.r1; q++) {
+        const uint32_t nchunks = 3u << (__ldg(&V.wshift[q]) - 2u);  // 3 r_i bytes / 16
+        const uint4 *row = V.bm + (size_t)__ldg(&V.line_off[q]) * 8u;
+        uint32_t cnt[PROBE_COLS];
+#pragma unroll
+        for (uint32_t b = 0; b < PROBE_COLS; b++) cnt[b] = 0;
+        for (uint32_t base = 0; base < nchunks; base += 32) {
+            const uint32_t k = base + lane;
+            const uint4 v = k < nchunks ? __ldg(row + k) : make_uint4(0, 0, 0, 0);
+            const uint32_t vw[4] = {v.x, v.y, v.z, v.w};
+            uint32_t cntw = 0;
+#pragma unroll
+            for (int j = 0; j < 16; j++) cntw += ((vw[j >> 2] >> (8 * (j & 3))) & 0x7Fu) ? 1u : 0u;
+            uint32_t incl = cntw;  // inclusive prefix sum over the warp
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t o = __shfl_up_sync(0xffffffffu, incl, d);
+                if (lane >= (uint32_t)d) incl += o;
+            }
+            const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+            uint32_t pos = incl - cntw;
+#pragma unroll
+            for (int j = 0; j < 16; j++) {
+                const uint32_t byte = (vw[j >> 2] >> (8 * (j & 3))) & 0xFFu;
+                if (byte & 0x7Fu) ent[pos++] = ((lane * 16u + (uint32_t)j) << 8) | byte;
+            }
+            __syncwarp();
+            for (uint32_t e = lane; e < total; e += 32) {
+                const uint32_t x = ent[e], byte = x & 0xFFu;
+                const uint32_t h = base * 16u + (x >> 8);  // byte offset in the row's BatMap
+                const uint32_t hs = h >> s, t = hs % 3u, low = h & r0m;
+                const uint32_t pi = (((byte & 0x7Fu) - 1u) << s) | low;
+                const uint64_t hj = ((uint64_t)(3u * ((pi & rcm) >> s) + t) << s) | low;
+#pragma unroll
+                for (uint32_t b = 0; b < PROBE_COLS; b++) {
+                    if (b < nc) {
+                        const uint32_t y = __ldg(col[b] + hj);
+                        cnt[b] += (((y ^ byte) & 0x7Fu) == 0u) & ((y | byte) >> 7);
+                    }
+                }
+            }
+            __syncwarp();
+        }
+#pragma unroll
+        for (uint32_t b = 0; b < PROBE_COLS; b++)
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) cnt[b] += __shfl_xor_sync(0xffffffffu, cnt[b], d);
+        uint32_t mine = 0;
+#pragma unroll
+        for (uint32_t b = 0; b < PROBE_COLS; b++)
+            if (lane == b) mine = cnt[b];
+        if (lane < nc) {
+            const uint32_t oi = __ldg(&V.order[q]), oj = __ldg(&V.order[wu.c0 + lane]);
+            V.C[support_index(oi, oj, n, V.n_a)] = mine;  // the unit owns these pairs
+        }
+    }
+}
+
+// Probe kernel: every warp pulls probe units from the queue until it is empty.
+__global__ void __launch_bounds__(256, 3)
+k_pair_probe(const InstView *__restrict__ views, const WorkUnit *__restrict__ units, uint32_t count,
+             uint32_t *__restrict__ counter, unsigned long long *stamps) {
+    __shared__ uint32_t s_ent[8][512];
+    const uint32_t lane = threadIdx.x & 31u;
+    uint32_t *ent = s_ent[threadIdx.x >> 5];
+    if (stamps && lane == 0) atomicMin(&stamps[0], (unsigned long long)global_ns());
+    for (;;) {
+        uint32_t u = 0;
+        if (lane == 0) u = atomicAdd(counter, 1u);
+        u = __shfl_sync(0xffffffffu, u, 0);
+        if (u >= count) break;
+        const WorkUnit wu = units[u];
+        probe_unit(views[wu.inst], wu, ent, lane);
+    }
+    if (stamps && lane == 0) atomicMax(&stamps[1], (unsigned long long)global_ns());
 }
 
 static size_t g_compare_smem = 0, g_small_smem = 0;
@@ -588,26 +708,40 @@ void prepare_compare() {
 #define X(i, a, b, c, d, e) small = std::max(small, Tile<a, b, c, d, e>::SMEM);
         BM_SMALL_LIST(X)
 #undef X
+#define X(i, a, b, c, d, e) small = std::max(small, DirectTile<a, b, c, d, e>::SMEM);
+        BM_DIRECT_SMALL_LIST(X)
+#undef X
         BM_CUDA(cudaFuncSetAttribute(k_compare_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)small));
         g_small_smem = small;
     }
 }
 
-bool small_shape(uint32_t shape) { return (shape & UNIT_SHAPE_MASK) >= 13; }
+bool small_shape(uint32_t shape) {
+    const uint32_t k = shape & UNIT_SHAPE_MASK;
+    return k >= 13 && k < (uint32_t)NUM_SHAPES;
+}
+bool probe_shape(uint32_t shape) { return (shape & UNIT_SHAPE_MASK) == PROBE_SHAPE; }
 
-void launch_compare(const InstView *d_views, const WorkUnit *d_units, uint32_t count, uint32_t nmain,
-                    uint32_t *d_counters, cudaStream_t st, unsigned long long *d_stamps) {
-    if (!count) return;
+void launch_compare(const InstView *d_views, const WorkUnit *d_units, UnitParts parts, uint32_t *d_counters,
+                    cudaStream_t st, unsigned long long *d_stamps, cudaEvent_t probe_start) {
     prepare_compare();
     const uint32_t sms = (uint32_t)device_sms();
-    if (nmain) {
-        k_compare<<<std::min(nmain, sms), 256, g_compare_smem, st>>>(d_views, d_units, nmain, d_counters, d_stamps);
+    if (parts.main) {
+        k_compare<<<std::min(parts.main, sms), 256, g_compare_smem, st>>>(d_views, d_units, parts.main, d_counters,
+                                                                         d_stamps);
         BM_CHECK_LAUNCH();
     }
-    if (count > nmain) {
-        k_compare_small<<<std::min(count - nmain, sms), 256, g_small_smem, st>>>(d_views, d_units + nmain,
-                                                                                count - nmain, d_counters + 1,
-                                                                                d_stamps);
+    if (parts.small) {
+        k_compare_small<<<std::min(parts.small, sms), 256, g_small_smem, st>>>(
+            d_views, d_units + parts.main, parts.small, d_counters + 1, d_stamps);
+        BM_CHECK_LAUNCH();
+    }
+    if (probe_start) BM_CUDA(cudaEventRecord(probe_start, st));
+    if (parts.probe) {
+        const uint32_t warps = 3u * 8u * sms;  // three 256-thread blocks per SM
+        const uint32_t blocks = (std::min(parts.probe, warps) + 7u) / 8u;
+        k_pair_probe<<<blocks, 256, 0, st>>>(d_views, d_units + parts.main + parts.small, parts.probe,
+                                             d_counters + 2, d_stamps);
         BM_CHECK_LAUNCH();
     }
 }
@@ -624,7 +758,8 @@ struct Tile2 {
 };
 
 // Tiles of the column class [cb, ce).  All pairs: the rows are every earlier
-// item, [0, c1 - 1).  Cross mode: the rows are the given range of the other
+// item from row_lo on, [row_lo, c1 - 1) (rows below row_lo are probed).
+// Cross mode: the rows are the given range [row_lo, row_hi) of the other
 // family (items no wider than the columns).  Tiles are listed in groups of
 // TILE_GROUP column strips, row strip by row strip inside a group, so the
 // tiles that run at the same time (consecutive in the queue) share row and
@@ -634,7 +769,7 @@ static void class_tiles(uint32_t cb, uint32_t ce, const ShapeDesc &sh, std::vect
                         bool cross = false, uint32_t row_lo = 0, uint32_t row_hi = 0) {
     for (uint32_t g0 = cb; g0 < ce; g0 += TILE_GROUP * sh.TC) {
         const uint32_t g1 = std::min(ce, g0 + TILE_GROUP * sh.TC);
-        const uint32_t lo = cross ? row_lo : 0, top = cross ? row_hi : g1 - 1;
+        const uint32_t lo = row_lo, top = cross ? row_hi : g1 - 1;
         for (uint32_t r0 = lo; r0 < top; r0 += sh.TR)
             for (uint32_t c0 = g0; c0 < g1; c0 += sh.TC) {
                 const uint32_t c1 = std::min(ce, c0 + sh.TC);
@@ -663,42 +798,101 @@ static void cross_rows(const batmap_set *S, uint32_t cb, uint32_t *lo, uint32_t 
     }
 }
 
+uint32_t probe_log_of(const batmap_params &p) {
+    if (p.probe_log >= 32) return 0;
+    return p.probe_log ? p.probe_log : PROBE_LOG_DEFAULT;
+}
+
+// Probe units of one column class: rows [lo, p) (all narrower than the
+// columns by 2^probe_log or more) against column chunks of at most
+// PROBE_COLS, widest rows first inside a chunk; rows are grouped into units
+// of about `target` probed words (row words x columns).
+static void probe_units(const batmap_set *S, uint32_t cb, uint32_t ce, uint32_t lo, uint32_t p, double target,
+                        std::vector<WorkUnit> *out) {
+    if (p <= lo || ce <= cb) return;
+    const uint32_t nc = ce - cb, nchunk = (nc + PROBE_COLS - 1) / PROBE_COLS, per = (nc + nchunk - 1) / nchunk;
+    for (uint32_t c0 = cb; c0 < ce; c0 += per) {
+        const uint32_t c1 = std::min(ce, c0 + per);
+        uint32_t r1 = p;
+        while (r1 > lo) {
+            uint32_t r0 = r1;
+            double cost = 0.0;
+            while (r0 > lo && (r0 == r1 || cost < target)) {
+                r0--;
+                cost += (double)words_of(S, r0) * (c1 - c0);
+            }
+            out->push_back({r0, r1, c0, c1, 0, 0, 0, PROBE_SHAPE | UNIT_WHOLE_K});
+            r1 = r0;
+        }
+    }
+}
+
+// Cost of probing one row word against one column, in the scheduler's
+// cost unit (a padded word pair of the 128 x 128 tile, shape efficiency 1):
+// on the m = 10^6, n = 2,000 Zipf workload the probe kernel reads 2.5e11 to
+// 3.4e11 row words (times columns) per second where the 128 x 128 tile
+// compares about 7e12 word pairs per second.
+constexpr double PROBE_WORD_COST = 24.0;
+
 void schedule_units(const batmap_set *S, uint32_t force_shape, const double *shape_eff,
                     double target_cost, std::vector<WorkUnit> *out) {
     const uint32_t ncls = (uint32_t)S->class_begin.size() - 1;
+    // Width-skewed rows of each class may go to the probe route (never when
+    // a shape is forced: the autotuner and the shape tests time the scan).
+    // Rows are sorted by width, so the probed rows are a prefix [lo, p) of
+    // the class's rows; p is chosen among the width boundaries of the rows
+    // eligible by probe_log so that probe cost + scan cost is least.
+    const uint32_t plog = force_shape ? 0 : probe_log_of(S->params);
+    std::vector<double> prefix(S->n + 1, 0.0);  // row words, sorted order
+    for (uint32_t q = 0; q < S->n; q++) prefix[q + 1] = prefix[q] + (double)words_of(S, q);
     struct Pick {
         uint32_t shape;
         std::vector<Tile2> tiles;
         uint64_t K;
     };
     std::vector<Pick> picks;
-    double total = 0.0;
+    struct ProbeRange {
+        uint32_t cb, ce, lo, p;
+    };
+    std::vector<ProbeRange> probes;
+    double total = 0.0, probe_total = 0.0;
     for (uint32_t c = 0; c < ncls; c++) {
         uint32_t cb = S->class_begin[c], ce = S->class_begin[c + 1];
         uint64_t K = words_of(S, cb);
+        uint32_t lo = 0, hi = cb;
+        if (S->n_a) cross_rows(S, cb, &lo, &hi);
+        uint32_t pmax = lo;
+        if (plog)
+            while (pmax < hi && S->wshift_sorted[pmax] + plog <= S->wshift_sorted[cb]) pmax++;
         Pick best{0, {}, K};
-        double best_cost = INFINITY;
-        for (uint32_t s = 0; s < (uint32_t)NUM_SHAPES; s++) {
-            if (force_shape && s + 1 != force_shape) continue;
-            if (!force_shape && S->params.shape_mask && !((S->params.shape_mask >> s) & 1u)) continue;
-            if (K % SHAPES[s].KC) continue;
-            std::vector<Tile2> tiles;
-            if (S->n_a) {
-                uint32_t lo, hi;
-                cross_rows(S, cb, &lo, &hi);
-                class_tiles(cb, ce, SHAPES[s], &tiles, true, lo, hi);
-            } else {
-                class_tiles(cb, ce, SHAPES[s], &tiles);
-            }
-            double cost = (double)tiles.size() * SHAPES[s].TR * SHAPES[s].TC * (double)K /
-                          (shape_eff ? shape_eff[s] : SHAPES[s].eff);
-            if (cost < best_cost) {
-                best_cost = cost;
-                best = Pick{s, std::move(tiles), K};
+        double best_cost = INFINITY, best_scan = 0.0, best_probe = 0.0;
+        uint32_t best_p = lo;
+        for (uint32_t p = lo; p <= pmax; p++) {
+            if (p > lo && p < pmax && S->wshift_sorted[p] == S->wshift_sorted[p - 1]) continue;
+            const double probe_cost = PROBE_WORD_COST * (double)(ce - cb) * (prefix[p] - prefix[lo]);
+            for (uint32_t s = 0; s < (uint32_t)NUM_SHAPES; s++) {
+                if (force_shape && s + 1 != force_shape) continue;
+                if (!force_shape && S->params.shape_mask && !((S->params.shape_mask >> s) & 1u)) continue;
+                if (K % SHAPES[s].KC) continue;
+                std::vector<Tile2> tiles;
+                class_tiles(cb, ce, SHAPES[s], &tiles, S->n_a != 0, p, hi);
+                const double scan_cost = (double)tiles.size() * SHAPES[s].TR * SHAPES[s].TC * (double)K /
+                                         (shape_eff ? shape_eff[s] : SHAPES[s].eff);
+                if (scan_cost + probe_cost < best_cost) {
+                    best_cost = scan_cost + probe_cost;
+                    best_scan = scan_cost;
+                    best_probe = probe_cost;
+                    best_p = p;
+                    best = Pick{s, std::move(tiles), K};
+                }
             }
         }
+        if (best_p > lo) {
+            probes.push_back({cb, ce, lo, best_p});
+            probe_total += best_probe / PROBE_WORD_COST;
+        }
         if (!best.tiles.empty()) {
-            total += best_cost;
+            total += best_scan;
             picks.push_back(std::move(best));
         }
     }
@@ -717,24 +911,55 @@ void schedule_units(const batmap_set *S, uint32_t force_shape, const double *sha
                                 (uint32_t)std::min<uint64_t>(klen, p.K - k0), 0,
                                 p.shape | (klen >= p.K ? UNIT_WHOLE_K : 0u)});
     }
+    // probe units: widest column classes first, about 8 units per warp of
+    // the probe kernel (three 256-thread blocks per SM)
+    const double probe_target = probe_total / (8.0 * 24.0 * device_sms());
+    for (auto it = probes.rbegin(); it != probes.rend(); ++it)
+        probe_units(S, it->cb, it->ce, it->lo, it->p, probe_target, out);
     sort_units(out);
 }
 
 double unit_cost(const WorkUnit &u) {
+    if (probe_shape(u.shape)) return 0.0;
     const ShapeDesc &sh = SHAPES[u.shape & UNIT_SHAPE_MASK];
     return (double)sh.TR * sh.TC * (double)u.klen / sh.eff;
 }
 
 void sort_units(std::vector<WorkUnit> *units) {
-    std::stable_sort(units->begin(), units->end(),
+    // probe units last, in the order they were listed; the rest longest first,
+    // the main shapes before the one-column shapes
+    auto mid = std::stable_partition(units->begin(), units->end(),
+                                     [](const WorkUnit &u) { return !probe_shape(u.shape); });
+    std::stable_sort(units->begin(), mid,
                      [](const WorkUnit &a, const WorkUnit &b) { return unit_cost(a) > unit_cost(b); });
-    std::stable_partition(units->begin(), units->end(), [](const WorkUnit &u) { return !small_shape(u.shape); });
+    std::stable_partition(units->begin(), mid, [](const WorkUnit &u) { return !small_shape(u.shape); });
 }
 
-uint32_t main_units(const std::vector<WorkUnit> &units) {
-    uint32_t k = 0;
-    while (k < units.size() && !small_shape(units[k].shape)) k++;
-    return k;
+UnitParts unit_parts(const std::vector<WorkUnit> &units) {
+    UnitParts p;
+    size_t k = 0;
+    while (k < units.size() && !small_shape(units[k].shape) && !probe_shape(units[k].shape)) k++;
+    p.main = (uint32_t)k;
+    while (k < units.size() && small_shape(units[k].shape)) k++;
+    p.small = (uint32_t)k - p.main;
+    p.probe = (uint32_t)(units.size() - k);
+    return p;
+}
+
+// Algorithmic work of the probe route in a unit list of one set: the
+// scan-equivalent word pairs it takes over (rows x columns x column words)
+// and the row words it reads (row words x columns).
+static void probe_stats(const batmap_set *S, const std::vector<WorkUnit> &units, double *word_pairs,
+                        double *words) {
+    double wp = 0.0, w = 0.0;
+    for (const WorkUnit &u : units) {
+        if (!probe_shape(u.shape)) continue;
+        const double nc = u.c1 - u.c0;
+        wp += (double)(u.r1 - u.r0) * nc * (double)words_of(S, u.c0);
+        for (uint32_t q = u.r0; q < u.r1; q++) w += (double)words_of(S, q) * nc;
+    }
+    *word_pairs = wp;
+    *words = w;
 }
 
 bool tuned_shape_eff(double *eff);  // batch.cu
@@ -744,6 +969,7 @@ void build_schedule(batmap_set *S) {
     double eff[NUM_SHAPES];
     const bool tuned = tuned_shape_eff(eff);
     schedule_units(S, S->params.tile, tuned ? eff : nullptr, 0.0, &S->units);
+    probe_stats(S, S->units, &S->probe_word_pairs, &S->probe_words);
     S->d_units.alloc(S->units.size());
     if (!S->units.empty())
         BM_CUDA(cudaMemcpyAsync(S->d_units.p, S->units.data(), S->units.size() * sizeof(WorkUnit),

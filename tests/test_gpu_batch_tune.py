@@ -32,7 +32,7 @@ def test_autotune_then_batch_exact():
         off, tids, perm = device_inputs(inst, q)
         sets.append(pkg.batmap_build(inst.m, off, tids, perm))
     eff = pkg.batmap_autotune(sets)
-    assert len(eff) == 16 and max(eff) == pytest.approx(1.0) and min(eff) > 0
+    assert len(eff) == pkg.NUM_SHAPES and max(eff) == pytest.approx(1.0) and min(eff) > 0
     fulls, bufs, refs = [], [], []
     for inst in insts:
         ref = oracle.pairs_full(inst.offsets, inst.tids, threads=os.cpu_count() or 4)

@@ -58,6 +58,13 @@ def test_dense_sizes(n):
     _check(datagen.zipf_tidlists(70_001, n, 0.05, seed=n, s=40))
 
 
+@pytest.mark.parametrize("m,n", [(20_000, 1500), (64, 600), (1000, 3000), (300_000, 520)])
+def test_dense_k_splits_and_block_counts(m, n):
+    """K ranges split over several CTAs with their partial sums added, a
+    single K step, more blocks than SMs, diagonal blocks at every position."""
+    _check(datagen.bernoulli_tidlists(m, n, 0.05, seed=m % 97 + n, s=3))
+
+
 def test_dense_empty_and_full_items():
     m = 5000
     lists = [[], np.arange(m, dtype=np.uint32), [], np.arange(0, m, 3, dtype=np.uint32), [7]]

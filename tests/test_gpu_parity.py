@@ -69,7 +69,7 @@ def test_zipf_mixed_widths_exact_and_valid(seed):
     assert layout_errors(inst, bset, seed) == []
 
 
-@pytest.mark.parametrize("tile", list(range(1, 17)))
+@pytest.mark.parametrize("tile", list(range(1, 19)))
 def test_every_tile_shape_exact(tile):
     import paper_1102_1003_gb300 as pkg
     inst = datagen.zipf_tidlists(40_000, 333, 0.04, seed=7, s=30)
@@ -232,3 +232,71 @@ def test_zipf_full_scale_exact():
     _check_exact(inst, full, n_out, pairs)
     info = bset.info
     assert info["n_classes"] >= 6
+
+
+def _skewed_instance(seed, n_wide=40, n_narrow=200, m=50_000):
+    """Two width groups far apart (wide items at 50%, narrow at 0.2% .. 2%):
+    every wide x narrow pair is width-skewed, the wide class has more columns
+    than one probe unit takes (PROBE_COLS = 16), and the narrow items span
+    several classes."""
+    rng = np.random.default_rng(seed)
+    lists = [np.flatnonzero(rng.random(m) < 0.5).astype(np.uint32) for _ in range(n_wide)]
+    lists += [np.flatnonzero(rng.random(m) < rng.uniform(0.002, 0.02)).astype(np.uint32)
+              for _ in range(n_narrow)]
+    order = rng.permutation(len(lists))  # original ids mixed across widths
+    return datagen.from_lists([lists[k] for k in order], m, s=20)
+
+
+@pytest.mark.parametrize("probe_log", [1, 2, 3, 5, 32])
+@pytest.mark.parametrize("params", [None, dict(max_loop=1, load_num=1, load_den=2)])
+def test_probe_route_exact(probe_log, params):
+    """The probe route (width-skewed pairs) and the cyclic scan give the same
+    supports at every threshold ratio, with and without failed insertions;
+    32 turns the route off."""
+    import paper_1102_1003_gb300 as pkg
+    for inst in (_skewed_instance(probe_log), datagen.zipf_tidlists(60_000, 300, 0.03, seed=probe_log, s=50)):
+        p = pkg.batmap_default_params(probe_log=probe_log, **(params or {}))
+        full, n_out, pairs, bset = run_all_pairs(inst, perm_seed=probe_log, params=p)
+        _check_exact(inst, full, n_out, pairs)
+        info = bset.info
+        if probe_log >= 32:
+            assert info["probe_word_pairs"] == 0
+        else:
+            assert info["probe_word_pairs"] > 0 and info["probe_words"] > 0
+            assert info["probe_word_pairs"] <= info["word_pairs"]
+        if params:
+            assert info["n_failed"] > 0
+
+
+def test_probe_route_cross_and_batch_exact():
+    """The probe route inside cross mode (family A rows against wide family B
+    columns and the reverse) and inside the batched form."""
+    import torch
+    import paper_1102_1003_gb300 as pkg
+    m = 40_000
+    rng = np.random.default_rng(8)
+    fam_a = [np.flatnonzero(rng.random(m) < p).astype(np.uint32) for p in rng.uniform(0.002, 0.6, 90)]
+    fam_b = [np.flatnonzero(rng.random(m) < p).astype(np.uint32) for p in rng.uniform(0.002, 0.6, 70)]
+    union = datagen.from_lists(fam_a + fam_b, m)
+    full_ref = oracle.pairs_full(union.offsets, union.tids, threads=THREADS)
+    a, b = np.meshgrid(np.arange(90), np.arange(70), indexing="ij")
+    ref_c = full_ref[oracle.packed_index(union.n, a.ravel(), 90 + b.ravel())].reshape(90, 70)
+    skew = _skewed_instance(9)
+    ref_s = oracle.pairs_full(skew.offsets, skew.tids, threads=THREADS)
+    p = pkg.batmap_default_params(probe_log=2)
+    o1, t1, _ = device_inputs(union, 1)
+    o2, t2, _ = device_inputs(skew, 2)
+    sets = [pkg.batmap_build_cross(m, 90, o1, t1, None, params=p), pkg.batmap_build(skew.m, o2, t2, None, params=p)]
+    assert sets[0].info["probe_word_pairs"] > 0 and sets[1].info["probe_word_pairs"] > 0
+    fulls = [torch.empty(90 * 70, dtype=torch.int32, device="cuda"),
+             torch.empty(ref_s.size, dtype=torch.int32, device="cuda")]
+    n_out, _ = pkg.pair_support_all(sets[0], 1, full=fulls[0])
+    assert np.array_equal(fulls[0].cpu().numpy().astype(np.uint32).reshape(90, 70), ref_c)
+    bufs = [torch.empty((int((ref_c >= 1).sum()), 3), dtype=torch.int32, device="cuda"),
+            torch.empty((max(1, int((ref_s >= skew.s).sum())), 3), dtype=torch.int32, device="cuda")]
+    for rep in range(2):
+        fulls[0].fill_(-1)
+        fulls[1].fill_(-1)
+        pkg.pair_support_batch(sets, [1, skew.s], bufs, fulls)
+        assert np.array_equal(fulls[0].cpu().numpy().astype(np.uint32).reshape(90, 70), ref_c), rep
+        assert np.array_equal(fulls[1].cpu().numpy().astype(np.uint32), ref_s), rep
