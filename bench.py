@@ -374,6 +374,10 @@ def plain_leg(inst, dev, steps, warmup, peaks, peak_kind, workload, sampler=None
     }
     if wp_probe > 0:
         probe_s = statistics.mean(probe_ms) / 1e3
+        rec["compare_equiv"] = {
+            "frac": OPS_PER_WORD_PAIR * wp / cmp_s / 1e12 / alu_peak,
+            "definition": "the whole compare step (scan + probe kernels) on the scan's work for every pair: "
+                          "4 x sum over pairs of max(|B_i|,|B_j|)/4 / compare time / lane-op peak"}
         rec["probe"] = {
             "kernel": "k_pair_probe", "ms": 1e3 * probe_s, "routed_word_pairs": wp_probe,
             "routed_share": wp_probe / wp, "words_read": info["probe_words"],
@@ -442,6 +446,7 @@ def run_mine(args, inst, rank, world):
     }
     if "probe" in rec:
         line["probe"] = rec["probe"]
+        line["compare_equiv"] = rec["compare_equiv"]
     if not args.no_dense and inst.m <= (1 << 24):
         line["dense"] = dense_leg(args, inst, off, tids, n_out, peaks, peak_kind, workload=label)
     del off, tids
