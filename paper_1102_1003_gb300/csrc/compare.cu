@@ -755,18 +755,28 @@ static inline uint64_t words_of(const batmap_set *S, uint32_t q) {
 
 struct Tile2 {
     uint32_t r0, r1, c0, c1;
+    uint32_t shape;  // 0-based shape index
 };
 
-// Tiles of the column class [cb, ce).  All pairs: the rows are every earlier
-// item from row_lo on, [row_lo, c1 - 1) (rows below row_lo are probed).
-// Cross mode: the rows are the given range [row_lo, row_hi) of the other
-// family (items no wider than the columns).  Tiles are listed in groups of
-// TILE_GROUP column strips, row strip by row strip inside a group, so the
-// tiles that run at the same time (consecutive in the queue) share row and
-// column strips and read them through L2 instead of each from DRAM.
+// Tiles of the column class [cb, ce) with primary shape `s`.  All pairs: the
+// rows are every earlier item from row_lo on, [row_lo, c1 - 1) (rows below
+// row_lo are probed).  Cross mode: the rows are the given range [row_lo,
+// row_hi) of the other family (items no wider than the columns).  Tiles are
+// listed in groups of TILE_GROUP column strips, row strip by row strip inside
+// a group, so the tiles that run at the same time (consecutive in the queue)
+// share row and column strips and read them through L2 instead of each from
+// DRAM.  A column tile's last, partial row strip may instead be covered by
+// tiles of a shorter-row shape of the same column width (`shorter`, each with
+// its cost per padded row), whichever pads least per unit of cost.
 constexpr uint32_t TILE_GROUP = 12;
-static void class_tiles(uint32_t cb, uint32_t ce, const ShapeDesc &sh, std::vector<Tile2> *out,
-                        bool cross = false, uint32_t row_lo = 0, uint32_t row_hi = 0) {
+struct RowOption {
+    uint32_t shape, TR;
+    double cost_per_row;  // 1 / shape efficiency
+};
+static void class_tiles(uint32_t cb, uint32_t ce, uint32_t s, const std::vector<RowOption> &shorter,
+                        double primary_cost_per_row, std::vector<Tile2> *out, bool cross = false,
+                        uint32_t row_lo = 0, uint32_t row_hi = 0) {
+    const ShapeDesc &sh = SHAPES[s];
     for (uint32_t g0 = cb; g0 < ce; g0 += TILE_GROUP * sh.TC) {
         const uint32_t g1 = std::min(ce, g0 + TILE_GROUP * sh.TC);
         const uint32_t lo = row_lo, top = cross ? row_hi : g1 - 1;
@@ -774,7 +784,21 @@ static void class_tiles(uint32_t cb, uint32_t ce, const ShapeDesc &sh, std::vect
             for (uint32_t c0 = g0; c0 < g1; c0 += sh.TC) {
                 const uint32_t c1 = std::min(ce, c0 + sh.TC);
                 const uint32_t hi = cross ? row_hi : c1 - 1;
-                if (r0 < hi) out->push_back({r0, std::min(hi, r0 + sh.TR), c0, c1});
+                if (r0 >= hi) continue;
+                const uint32_t r1 = std::min(hi, r0 + sh.TR), rows = r1 - r0;
+                // cheapest cover of a partial strip: the primary tile or k shorter tiles
+                uint32_t best = s, best_tr = sh.TR;
+                double best_cost = primary_cost_per_row * sh.TR;
+                if (rows < sh.TR)
+                    for (const RowOption &o : shorter) {
+                        const double c = (double)((rows + o.TR - 1) / o.TR) * o.TR * o.cost_per_row;
+                        if (c < best_cost) {
+                            best_cost = c;
+                            best = o.shape;
+                            best_tr = o.TR;
+                        }
+                    }
+                for (uint32_t a = r0; a < r1; a += best_tr) out->push_back({a, std::min(r1, a + best_tr), c0, c1, best});
             }
     }
 }
@@ -867,17 +891,26 @@ void schedule_units(const batmap_set *S, uint32_t force_shape, const double *sha
         Pick best{0, {}, K};
         double best_cost = INFINITY, best_scan = 0.0, best_probe = 0.0;
         uint32_t best_p = lo;
+        auto allowed = [&](uint32_t s) {
+            if (force_shape) return s + 1 == force_shape;
+            if (S->params.shape_mask && !((S->params.shape_mask >> s) & 1u)) return false;
+            return K % SHAPES[s].KC == 0;
+        };
+        auto eff_of = [&](uint32_t s) { return shape_eff ? shape_eff[s] : SHAPES[s].eff; };
         for (uint32_t p = lo; p <= pmax; p++) {
             if (p > lo && p < pmax && S->wshift_sorted[p] == S->wshift_sorted[p - 1]) continue;
             const double probe_cost = PROBE_WORD_COST * (double)(ce - cb) * (prefix[p] - prefix[lo]);
             for (uint32_t s = 0; s < (uint32_t)NUM_SHAPES; s++) {
-                if (force_shape && s + 1 != force_shape) continue;
-                if (!force_shape && S->params.shape_mask && !((S->params.shape_mask >> s) & 1u)) continue;
-                if (K % SHAPES[s].KC) continue;
+                if (!allowed(s)) continue;
+                std::vector<RowOption> shorter;  // same column width, fewer rows (never when forced)
+                for (uint32_t f = 0; f < (uint32_t)NUM_SHAPES && !force_shape; f++)
+                    if (allowed(f) && SHAPES[f].TC == SHAPES[s].TC && SHAPES[f].TR < SHAPES[s].TR)
+                        shorter.push_back({f, SHAPES[f].TR, 1.0 / eff_of(f)});
                 std::vector<Tile2> tiles;
-                class_tiles(cb, ce, SHAPES[s], &tiles, S->n_a != 0, p, hi);
-                const double scan_cost = (double)tiles.size() * SHAPES[s].TR * SHAPES[s].TC * (double)K /
-                                         (shape_eff ? shape_eff[s] : SHAPES[s].eff);
+                class_tiles(cb, ce, s, shorter, 1.0 / eff_of(s), &tiles, S->n_a != 0, p, hi);
+                double scan_cost = 0.0;
+                for (const Tile2 &t : tiles)
+                    scan_cost += (double)SHAPES[t.shape].TR * SHAPES[t.shape].TC * (double)K / eff_of(t.shape);
                 if (scan_cost + probe_cost < best_cost) {
                     best_cost = scan_cost + probe_cost;
                     best_scan = scan_cost;
@@ -898,18 +931,25 @@ void schedule_units(const batmap_set *S, uint32_t force_shape, const double *sha
     }
     if (target_cost <= 0.0) target_cost = total / (8.0 * device_sms());
     for (auto &p : picks) {
-        const ShapeDesc &sh = SHAPES[p.shape];
-        const double tile_cost = (double)sh.TR * sh.TC * (double)p.K;
-        uint64_t nk = (uint64_t)std::ceil(tile_cost / std::max(target_cost, 1.0));
-        nk = std::max<uint64_t>(1, std::min<uint64_t>(nk, p.K / sh.KC));
-        uint64_t klen = (p.K + nk - 1) / nk;
-        klen = (klen + sh.KC - 1) / sh.KC * sh.KC;
-        klen = std::min<uint64_t>(klen, 1ull << 22);  // 128 * 4 * klen < 2^32
-        for (const Tile2 &t : p.tiles)
+        // the K split of each shape in the pick: units of about target_cost
+        uint64_t klen_of[NUM_SHAPES] = {};
+        for (const Tile2 &t : p.tiles) {
+            if (klen_of[t.shape]) continue;
+            const ShapeDesc &sh = SHAPES[t.shape];
+            const double tile_cost = (double)sh.TR * sh.TC * (double)p.K;
+            uint64_t nk = (uint64_t)std::ceil(tile_cost / std::max(target_cost, 1.0));
+            nk = std::max<uint64_t>(1, std::min<uint64_t>(nk, p.K / sh.KC));
+            uint64_t klen = (p.K + nk - 1) / nk;
+            klen = (klen + sh.KC - 1) / sh.KC * sh.KC;
+            klen_of[t.shape] = std::min<uint64_t>(klen, 1ull << 22);  // 128 * 4 * klen < 2^32
+        }
+        for (const Tile2 &t : p.tiles) {
+            const uint64_t klen = klen_of[t.shape];
             for (uint64_t k0 = 0; k0 < p.K; k0 += klen)
                 out->push_back({t.r0, t.r1, t.c0, t.c1, (uint32_t)k0,
                                 (uint32_t)std::min<uint64_t>(klen, p.K - k0), 0,
-                                p.shape | (klen >= p.K ? UNIT_WHOLE_K : 0u)});
+                                t.shape | (klen >= p.K ? UNIT_WHOLE_K : 0u)});
+        }
     }
     // probe units: widest column classes first, about 8 units per warp of
     // the probe kernel (three 256-thread blocks per SM)
