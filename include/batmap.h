@@ -318,7 +318,9 @@ batmap_status pair_support_all(batmap_set *set, uint32_t s, uint32_t *d_pairs, u
  *       memory gives the fastest copies); h_perm may be NULL (computed
  *       permutations, nothing to copy).
  *   h_pairs, cap, n_out : host output triples as in pair_support_all.
- * Synchronises the stream; device memory is released before returning.
+ * Synchronises the stream.  The device copies of the inputs and of the output
+ * are kept by the library for the next call (grown when a call needs more)
+ * until batmap_release_scratch; calls from several threads are serialised.
  */
 batmap_status pair_support_host(const batmap_params *p, uint32_t m, uint32_t n,
                                 const uint64_t *h_offsets, const uint32_t *h_tids,
@@ -362,7 +364,8 @@ batmap_status batmap_get_timing(const batmap_set *set, batmap_timing *t);
 
 /* Release the scratch the library caches between calls (the placement table
  * of batmap_build, one uint32 per BatMap byte; the dense path's bitmap and
- * workspace).  Call when no other call of the library is running. */
+ * workspace; pair_support_host's device copies of its inputs and output).
+ * Call when no other call of the library is running. */
 void batmap_release_scratch(void);
 
 /* Number of kernels this library has launched in the process so far (a

@@ -1,6 +1,7 @@
 // The extern "C" boundary: argument checks, error translation, and the
 // orchestration of build -> compare -> correct -> compact on one stream.
 #include <atomic>
+#include <mutex>
 #include <cstring>
 #include <new>
 #include <string>
@@ -33,6 +34,23 @@ void release_dense_workspace();
 void release_batch_plan();
 
 static std::atomic<uint64_t> g_gen{1};
+
+// Workspace of pair_support_host: device copies of the caller's host inputs and the pair
+// output, grown as needed and released by batmap_release_scratch.
+struct HostPathWork {
+    DevBuf<uint64_t> off;
+    DevBuf<uint32_t> tids, perm, pairs;
+};
+static std::mutex g_host_mu;
+static HostPathWork g_host_work;
+
+void release_host_workspace() {
+    std::lock_guard<std::mutex> lock(g_host_mu);
+    g_host_work.off.release();
+    g_host_work.tids.release();
+    g_host_work.perm.release();
+    g_host_work.pairs.release();
+}
 
 template <typename F>
 static batmap_status guarded(F &&f) {
@@ -263,27 +281,31 @@ batmap_status pair_support_host(const batmap_params *p, uint32_t m, uint32_t n, 
         BM_REQUIRE(h_offsets && n_out, BATMAP_ERR_ARG, "NULL argument");
         BM_REQUIRE(cap == 0 || h_pairs, BATMAP_ERR_ARG, "h_pairs is NULL with cap > 0");
         const uint64_t T = h_offsets[n];
-        DevBuf<uint64_t> d_off(n + 1);
-        DevBuf<uint32_t> d_tids(T), d_perm(h_perm ? 3ull * m : 0), d_pairs(3 * cap);
-        BM_CUDA(cudaMemcpyAsync(d_off.p, h_offsets, (n + 1) * 8ull, cudaMemcpyHostToDevice, st));
-        if (T) BM_CUDA(cudaMemcpyAsync(d_tids.p, h_tids, T * 4ull, cudaMemcpyHostToDevice, st));
-        if (h_perm) BM_CUDA(cudaMemcpyAsync(d_perm.p, h_perm, 3ull * m * 4, cudaMemcpyHostToDevice, st));
+        // device copies of the inputs and the output, kept for the next call (each call ends
+        // with a stream synchronisation; calls are serialised on the workspace)
+        std::lock_guard<std::mutex> lock(g_host_mu);
+        HostPathWork &W = g_host_work;
+        W.off.ensure(n + 1);
+        W.tids.ensure(T);
+        if (h_perm) W.perm.ensure(3ull * m);
+        W.pairs.ensure(3 * cap);
+        BM_CUDA(cudaMemcpyAsync(W.off.p, h_offsets, (n + 1) * 8ull, cudaMemcpyHostToDevice, st));
+        if (T) BM_CUDA(cudaMemcpyAsync(W.tids.p, h_tids, T * 4ull, cudaMemcpyHostToDevice, st));
+        if (h_perm) BM_CUDA(cudaMemcpyAsync(W.perm.p, h_perm, 3ull * m * 4, cudaMemcpyHostToDevice, st));
         batmap_set *S = nullptr;
-        batmap_status rc = batmap_build(p, m, n, d_off.p, d_tids.p, h_perm ? d_perm.p : nullptr, st, &S);
+        batmap_status rc = batmap_build(p, m, n, W.off.p, W.tids.p, h_perm ? W.perm.p : nullptr, st, &S);
         if (rc != BATMAP_OK) throw Error{rc, g_last_error};
-        d_off.release();
-        d_tids.release();
-        d_perm.release();
+        uint32_t *d_pairs = W.pairs.p;
         std::string msg;
         try {
             uint64_t total = 0;
-            rc = pair_support_all(S, s, d_pairs.p, cap, &total, nullptr, st);
+            rc = pair_support_all(S, s, d_pairs, cap, &total, nullptr, st);
             msg = g_last_error;
             *n_out = total;
             if (rc != BATMAP_OK && rc != BATMAP_ERR_CAPACITY) throw Error{rc, msg};
             uint64_t ncopy = std::min<uint64_t>(total, cap);
             if (ncopy)
-                BM_CUDA(cudaMemcpyAsync(h_pairs, d_pairs.p, ncopy * 12ull, cudaMemcpyDeviceToHost, st));
+                BM_CUDA(cudaMemcpyAsync(h_pairs, d_pairs, ncopy * 12ull, cudaMemcpyDeviceToHost, st));
             BM_CUDA(cudaStreamSynchronize(st));
         } catch (...) {
             batmap_free(S);
@@ -306,6 +328,7 @@ uint64_t batmap_kernel_launches(void) { return g_launches.load(); }
 void batmap_release_scratch(void) {
     release_scratch();
     release_dense_workspace();
+    release_host_workspace();
 }
 
 static void require_pair_sets(batmap_set *const *sets, uint32_t k) {
