@@ -10,7 +10,11 @@
 // of Sec. V): membership in a BatMap is two byte probes -- x is stored in two
 // of the three tables, so tables 1 and 2 always hold at least one copy -- plus
 // a binary search of the set's failed insertions; a set without a BatMap is
-// binary-searched.
+// searched in two levels: a sampled index of every IDX_STRIDE-th tid of each
+// set (1/64 of the tidlists, small enough that its upper levels stay in L2)
+// narrows the search to one block of IDX_STRIDE tids (256 contiguous bytes),
+// so a membership test takes about two dependent DRAM reads instead of one per
+// level of a binary search over the whole tidlist.
 //
 // Work is cut into tasks of up to 1024 elements of the smallest set; one warp
 // runs a task and adds its count with one atomic.
@@ -30,6 +34,7 @@ void build_set(batmap_set *S, const uint64_t *d_offsets, const uint32_t *d_tids,
 
 constexpr uint32_t TASK_ELEMS = 1024;
 constexpr uint32_t MAX_K = 8;
+constexpr uint32_t IDX_STRIDE = 64;  // tids per block of the sampled index
 
 struct QueryDesc {
     uint32_t k;
@@ -52,6 +57,8 @@ struct PoolView {
     const uint32_t *f_tid;
     const uint8_t *bm;        // BatMap bytes
     uint32_t m, shift;
+    const uint64_t *idx_off;  // [n+1] sampled index: ceil(|S_c| / IDX_STRIDE) entries per set
+    const uint32_t *idx;      // entry j of set c = tid IDX_STRIDE * j of set c
 };
 
 __device__ __forceinline__ bool bsearch_u32(const uint32_t *a, uint64_t lo, uint64_t hi, uint32_t x) {
@@ -64,9 +71,26 @@ __device__ __forceinline__ bool bsearch_u32(const uint32_t *a, uint64_t lo, uint
     return false;
 }
 
+// x in set c's sorted tidlist: the last index entry <= x names the block of
+// IDX_STRIDE tids that can hold x; that block is binary-searched.
+__device__ __forceinline__ bool tidlist_member(const PoolView &P, uint32_t c, uint32_t x) {
+    const uint64_t i0 = P.idx_off[c];
+    uint64_t lo = i0, hi = P.idx_off[c + 1];
+    while (lo < hi) {  // first entry > x
+        const uint64_t mid = (lo + hi) >> 1;
+        const uint32_t v = P.idx[mid];
+        if (v == x) return true;
+        if (v < x) lo = mid + 1; else hi = mid;
+    }
+    if (lo == i0) return false;  // x below the set's first tid
+    const uint64_t s0 = P.off[c], first = s0 + (uint64_t)IDX_STRIDE * (lo - 1 - i0);
+    const uint64_t end = min(P.off[c + 1], first + IDX_STRIDE);
+    return bsearch_u32(P.tids, first + 1, end, x);  // the block's first tid is the entry, != x
+}
+
 __device__ __forceinline__ bool member(const PoolView &P, uint32_t c, uint32_t x) {
     const int32_t b = P.bm_index[c];
-    if (b < 0) return bsearch_u32(P.tids, P.off[c], P.off[c + 1], x);
+    if (b < 0) return tidlist_member(P, c, x);
     const uint64_t base = P.bm_base[b];
     const uint32_t r = 1u << P.bm_rlog[b];
 #pragma unroll
@@ -157,6 +181,15 @@ __global__ void k_query_offsets(const uint64_t *__restrict__ task_off, const uin
     if (q <= nq) out_off[q] = task_off[first_task[q]];
 }
 
+// The sampled index: entry j of set c is tid IDX_STRIDE * j of set c.
+__global__ void k_sample_index(const uint64_t *__restrict__ off, const uint32_t *__restrict__ tids, uint32_t n,
+                               const uint64_t *__restrict__ idx_off, uint32_t *__restrict__ idx) {
+    for (uint32_t c = blockIdx.x; c < n; c += gridDim.x) {
+        const uint64_t b = off[c], k0 = idx_off[c], nk = idx_off[c + 1] - k0;
+        for (uint64_t j = threadIdx.x; j < nk; j += blockDim.x) idx[k0 + j] = tids[b + (uint64_t)IDX_STRIDE * j];
+    }
+}
+
 // One warp per set: every tid < m and strictly increasing within its set.
 __global__ void k_validate_sets(const uint64_t *__restrict__ off, const uint32_t *__restrict__ tids, uint32_t n,
                                 uint32_t m, int *err) {
@@ -186,6 +219,8 @@ struct batmap_pool {
     DevBuf<uint64_t> d_bm_base, d_fail_off;
     DevBuf<uint32_t> d_bm_rlog, d_fail_tid;
     DevBuf<uint8_t> d_bm;
+    DevBuf<uint64_t> d_idx_off;  // sampled index of the tidlists
+    DevBuf<uint32_t> d_idx;
     uint32_t n_big = 0, shift = 0;
     uint64_t bm_bytes = 0, n_failed = 0;
     PoolView view{};
@@ -226,6 +261,21 @@ static void pool_create(const batmap_params *p, uint32_t m, uint32_t n, const ui
         BM_CUDA(cudaMemcpyAsync(&h, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
         BM_CUDA(cudaStreamSynchronize(st));
         BM_REQUIRE(h == 0, BATMAP_ERR_ARG, "tids must be strictly increasing per set and < m");
+    }
+
+    // the sampled index of every tidlist (all sets: BatMap-backed ones keep it too)
+    {
+        std::vector<uint64_t> ioff(n + 1, 0);
+        for (uint32_t i = 0; i < n; i++)
+            ioff[i + 1] = ioff[i] + (pool->h_off[i + 1] - pool->h_off[i] + IDX_STRIDE - 1) / IDX_STRIDE;
+        pool->d_idx_off.alloc(n + 1);
+        pool->d_idx.alloc(std::max<uint64_t>(ioff[n], 1));
+        BM_CUDA(cudaMemcpyAsync(pool->d_idx_off.p, ioff.data(), (n + 1) * 8ull, cudaMemcpyHostToDevice, st));
+        if (ioff[n]) {
+            k_sample_index<<<(unsigned)std::min<uint32_t>(std::max<uint32_t>(n, 1), 65535), 256, 0, st>>>(
+                pool->d_off.p, pool->d_tids.p, n, pool->d_idx_off.p, pool->d_idx.p);
+            BM_CHECK_LAUNCH();
+        }
     }
 
     // sets whose 8-bit BatMap is compact: c |S| >= r_0
@@ -330,7 +380,8 @@ static void pool_create(const batmap_params *p, uint32_t m, uint32_t n, const ui
     pool->view = PoolView{pool->d_off.p,     pool->d_tids.p,     make_perm_view(d_perm ? pool->d_perm.p : nullptr, m, P.perm_seed),
                           pool->d_bm_index.p, pool->d_bm_base.p, pool->d_bm_rlog.p,
                           pool->d_fail_off.p, pool->d_fail_tid.p, pool->d_bm.p,
-                          m,                  nb ? pool->shift : shift};
+                          m,                  nb ? pool->shift : shift,
+                          pool->d_idx_off.p,  pool->d_idx.p};
     BM_CUDA(cudaStreamSynchronize(st));
     *out = pool.release();
 }
