@@ -25,7 +25,7 @@ int device_sms();
 // Build the compare work units of one set (fills S->units, longest first,
 // and uploads them).  `shape_eff` (NULL = built-in prior) gives the relative
 // throughput of each shape (autotuner); `force_shape` (1..NUM_SHAPES) pins
-// one shape; target_cost <= 0 picks about 8 units per SM.
+// one shape; target_cost <= 0 picks about 32 units per SM.
 void build_schedule(batmap_set *S);
 void schedule_units(const batmap_set *S, uint32_t force_shape, const double *shape_eff,
                     double target_cost, std::vector<WorkUnit> *out);
