@@ -961,12 +961,20 @@ void schedule_units(const batmap_set *S, uint32_t force_shape, const double *sha
             klen = (klen + sh.KC - 1) / sh.KC * sh.KC;
             klen_of[t.shape] = std::min<uint64_t>(klen, 1ull << 22);  // 128 * 4 * klen < 2^32
         }
-        for (const Tile2 &t : p.tiles) {
-            const uint64_t klen = klen_of[t.shape];
-            for (uint64_t k0 = 0; k0 < p.K; k0 += klen)
+        // K piece by K piece, each over the tiles in their grouped order, so that the
+        // units running at the same time are neighbouring tiles over the same words
+        // (they share row and column strips through L2)
+        for (uint64_t piece = 0;; piece++) {
+            bool any = false;
+            for (const Tile2 &t : p.tiles) {
+                const uint64_t klen = klen_of[t.shape], k0 = piece * klen;
+                if (k0 >= p.K) continue;
+                any = true;
                 out->push_back({t.r0, t.r1, t.c0, t.c1, (uint32_t)k0,
                                 (uint32_t)std::min<uint64_t>(klen, p.K - k0), 0,
                                 t.shape | (klen >= p.K ? UNIT_WHOLE_K : 0u)});
+            }
+            if (!any) break;
         }
     }
     // probe units: widest column classes first, about 8 units per warp of
