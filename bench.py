@@ -869,6 +869,115 @@ def run_triples(args):
     print(json.dumps(line), flush=True)
 
 
+def run_quads(args):
+    """Frequent itemsets of size 4 (Apriori level 4) over 4-of-5 BatMaps: one step =
+    2-of-3 build + frequent pairs + 4-of-5 build + frequent triples + frequent
+    quadruples (candidates, witness supports, compaction), tidlists resident in HBM."""
+    import torch
+    import paper_1102_1003_gb300 as pkg
+    import oracle
+    from oracle import dof_rules as R
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    L = pkg.load_library()
+    inst = datagen.triples_instance()
+    s = inst.s
+    off = torch.from_numpy(inst.offsets.view(np.int64)).to(dev)
+    tids = torch.from_numpy(inst.tids.view(np.int32)).to(dev)
+    b2 = pkg.batmap_build(inst.m, off, tids, None)
+    n_pairs, pairs = pkg.pair_support_all(b2, s)
+    pairs_buf = torch.empty((max(n_pairs, 1), 3), dtype=torch.int32, device=dev)
+    b2.free()
+    b4 = pkg.batmap_build_d(4, inst.m, off, tids, None)
+    n_trip, trip, n_c3 = pkg.frequent_triples(b4, s, pairs)
+    trip_buf = torch.empty((max(n_trip, 1), 4), dtype=torch.int32, device=dev)
+    n_quad, quad, n_c4 = pkg.frequent_quadruples(b4, s, trip)
+    quad_buf = torch.empty((max(n_quad, 1), 5), dtype=torch.int32, device=dev)
+    info4 = b4.info
+    b4.free()
+
+    def step():
+        a = pkg.batmap_build(inst.m, off, tids, None)
+        k2, p = pkg.pair_support_all(a, s, pairs=pairs_buf)
+        t2 = pkg.batmap_get_timing(a)
+        a.free()
+        b = pkg.batmap_build_d(4, inst.m, off, tids, None)
+        tb = pkg.batmap_get_timing(b)
+        k3, t, c3 = pkg.frequent_triples(b, s, p, out=trip_buf)
+        t3 = pkg.batmap_get_timing(b)
+        k4, q, c4 = pkg.frequent_quadruples(b, s, t, out=quad_buf)
+        t4 = pkg.batmap_get_timing(b)
+        b.free()
+        return k2, k3, k4, c4, t2, tb, t3, t4
+
+    for _ in range(args.warmup):
+        step()
+    stream = torch.cuda.current_stream()
+    sampler = ClockSampler(0)
+    sampler.start()
+    torch.cuda.synchronize()
+    launches0 = L.batmap_kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    rec = [step() for _ in range(args.steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    launches = L.batmap_kernel_launches() - launches0
+    clocks = sampler.stop()
+    assert all(r[0] == n_pairs and r[1] == n_trip and r[2] == n_quad and r[3] == n_c4 for r in rec)
+    # parity: the frequent pairs in full; sampled triple and quadruple candidates against the oracle
+    pairs_ref = oracle.pairs_threshold(inst.offsets, inst.tids, s)
+    exact_pairs = bool(np.array_equal(pairs_buf[:n_pairs].cpu().numpy().astype(np.uint32), pairs_ref))
+    rng = np.random.default_rng(4)
+    got3 = trip_buf[:n_trip].cpu().numpy().astype(np.uint32)
+    got4 = quad_buf[:n_quad].cpu().numpy().astype(np.uint32)
+
+    def sampled_ok(cands, got, width):
+        pick = rng.choice(cands.shape[0], min(2000, cands.shape[0]), replace=False)
+        sup = oracle.kway_counts(inst.offsets, inst.tids, cands[pick].tolist())
+        keep = {tuple(x[:width]): x[width] for x in got.tolist()}
+        return all(((tuple(c) in keep) == (v >= s)) and (v < s or keep[tuple(c)] == v)
+                   for c, v in zip(cands[pick].tolist(), sup.tolist())), int(pick.size)
+
+    c3 = R.triple_candidates(pairs_ref[:, :2])
+    ok3, k3 = sampled_ok(c3, got3, 3)
+    c4 = R.quadruple_candidates(got3[:, :3]) if n_trip else np.zeros((0, 4), np.int64)
+    ok4, k4 = sampled_ok(c4, got4, 4) if c4.shape[0] else (True, 0)
+    line = {"metric": "candidate itemset supports/sec (Apriori levels 3 and 4 over 4-of-5 BatMaps), bit-exact",
+            "workload": "quads", "unit": "candidate-supports/s", "value": (n_c3 + n_c4) * args.steps / elapsed,
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": "quads", "m": inst.m, "n": inst.n, "s": s, "tids": int(inst.tids.size),
+                       "desc": "Zipf(1) items at mean density 2%", "frequent_pairs": n_pairs,
+                       "triple_candidates": n_c3, "frequent_triples": n_trip,
+                       "quadruple_candidates": n_c4, "frequent_quadruples": n_quad,
+                       "batmap4_bytes": int(info4["bytes"])},
+            "phases_ms": {"build_2of3": statistics.mean(r[4]["build_ms"] for r in rec),
+                          "pairs": statistics.mean(r[4]["pairs_ms"] for r in rec),
+                          "build_4of5": statistics.mean(r[5]["build_ms"] for r in rec),
+                          "triples": statistics.mean(r[6]["pairs_ms"] for r in rec),
+                          "triple_witness_scan": statistics.mean(r[6]["scan_ms"] for r in rec),
+                          "triple_witness_probe": statistics.mean(r[6]["probe_ms"] for r in rec),
+                          "quadruples": statistics.mean(r[7]["pairs_ms"] for r in rec),
+                          "quadruple_witness": statistics.mean(r[7]["compare_ms"] for r in rec),
+                          "quadruple_witness_scan": statistics.mean(r[7]["scan_ms"] for r in rec),
+                          "quadruple_witness_probe": statistics.mean(r[7]["probe_ms"] for r in rec)},
+            "gpu_launches": int(launches), "failed_insertions_4of5": info4["n_failed"],
+            "parity": {"pairs_exact": exact_pairs, "sampled_triple_candidates": k3, "triples_exact": bool(ok3),
+                       "sampled_quadruple_candidates": k4, "quadruples_exact": bool(ok4)},
+            "clocks": clocks}
+    if not args.no_cpu_baseline and c4.shape[0]:
+        k = 2000
+        t0 = time.perf_counter()
+        oracle.kway_counts(inst.offsets, inst.tids, c4[rng.choice(c4.shape[0], k)].tolist())
+        dt = max(time.perf_counter() - t0, 1e-6)
+        line["cpu_baseline"] = {"value": k / dt, "unit": "candidate-supports/s", "cores": 1, "kind": "oracle",
+                                "sample": f"{k} uniformly sampled quadruple candidates, single-threaded k-way "
+                                          f"merge, {dt:.1f} s"}
+    print(json.dumps(line), flush=True)
+
+
 def run_serve(args):
     """Serving workload: pool of sets over 2^26 with Zipf sizes on [10, 1e6],
     Poisson-arriving queries (80% pairs, 20% 3..8-way), continuous batching."""
@@ -953,7 +1062,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["mine", "reference"], default="mine")
-    ap.add_argument("--workload", choices=sorted(WORKLOAD_DESC) + ["serve", "batch", "nsweep", "cross", "triples"], default="bern_m4m_n8192_p5")
+    ap.add_argument("--workload", choices=sorted(WORKLOAD_DESC) + ["serve", "batch", "nsweep", "cross", "triples", "quads"], default="bern_m4m_n8192_p5")
     ap.add_argument("--nsweep", type=int, nargs="+", default=[1000, 2000, 4000, 8000, 16000, 32000, 64000])
     ap.add_argument("--instances", type=int, default=64, help="instances (batch workload)")
     ap.add_argument("--batch-small", action="store_true",
@@ -978,10 +1087,10 @@ def main():
     PROBE_LOG = args.probe_log
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
-    if args.workload in ("serve", "batch", "nsweep", "cross", "triples"):
+    if args.workload in ("serve", "batch", "nsweep", "cross", "triples", "quads"):
         if rank == 0:
             {"serve": run_serve, "batch": run_batch, "nsweep": run_nsweep, "cross": run_cross,
-             "triples": run_triples}[args.workload](args)
+             "triples": run_triples, "quads": run_quads}[args.workload](args)
         return
     inst = datagen.workload_instance(args.workload, scale_n=args.scale_n, workers=os.cpu_count() or 8)
     if args.impl == "reference":

@@ -453,22 +453,43 @@ __device__ __forceinline__ uint32_t failed_common(const View &V, const uint32_t 
 // reads word w = w0 + l of every BatMap, the narrower ones cyclically (w mod
 // the width NT r_i / 4 words: block-wise, Fig. 1); 32 consecutive words lie
 // in one table because a table block is r_0 >= 128 bytes.
+// Width-skewed tuples go to a probe kernel instead of the scan: when the
+// widest of the BatMaps is at least 2^PROBE_LOG times the narrowest, the scan
+// (which runs over the widest) costs more than visiting the narrowest one's
+// slots and probing the others (a same-box sweep of the frequent-triples
+// step put the best threshold at 8x).
+constexpr uint32_t PROBE_LOG = 3;
+template <int K>
+__device__ __forceinline__ bool probe_route_k(const uint32_t (&lg)[K]) {
+    uint32_t lo = lg[0], hi = lg[0];
+#pragma unroll
+    for (int j = 1; j < K; j++) {
+        lo = min(lo, lg[j]);
+        hi = max(hi, lg[j]);
+    }
+    return hi - lo >= PROBE_LOG;
+}
+
+// skip_routed: leave the width-skewed queries (probe_route_k) to
+// k_witness_probe_k, which writes their supports.
 template <int K, uint32_t NT>
 __global__ void __launch_bounds__(256) k_witness(View V, const uint32_t *__restrict__ items, uint64_t nq,
-                                                 uint32_t *__restrict__ out) {
+                                                 uint32_t *__restrict__ out, uint32_t skip_routed) {
     const uint32_t lane = threadIdx.x & 31u;
     const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x / 32);
     for (uint64_t q = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) / 32; q < nq; q += nwarps) {
-        uint32_t it[K], e[K];
+        uint32_t it[K], e[K], lg[K];
         uint64_t wb[K];
         uint32_t wmax = 0;
 #pragma unroll
         for (int j = 0; j < K; j++) {
             it[j] = __ldg(&items[q * K + j]);
-            e[j] = V.rlog[it[j]] - 2;  // 2^e words per table segment of a block run
+            lg[j] = V.rlog[it[j]];
+            e[j] = lg[j] - 2;  // 2^e words per table segment of a block run
             wb[j] = V.base[it[j]] >> 2;
             wmax = max(wmax, NT << e[j]);
         }
+        if (skip_routed && probe_route_k<K>(lg)) continue;
         const uint32_t tshift = V.shift - 2;  // words per table block = r_0 / 4
         uint32_t cnt = 0;
         for (uint32_t w = lane; w < wmax; w += 32) {
@@ -486,6 +507,113 @@ __global__ void __launch_bounds__(256) k_witness(View V, const uint32_t *__restr
 #pragma unroll
         for (int d = 16; d > 0; d >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, d);
         if (lane == 0) out[q] = cnt;
+    }
+}
+
+// Indices of the queries of K items routed to the probe kernel (any order).
+template <int K>
+__global__ void k_route_probe_k(const uint32_t *__restrict__ items, uint64_t nq, const uint32_t *__restrict__ rlog,
+                                uint32_t *__restrict__ list, unsigned long long *__restrict__ count) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nq; i += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t lg[K];
+#pragma unroll
+        for (int j = 0; j < K; j++) lg[j] = rlog[items[K * i + j]];
+        if (probe_route_k<K>(lg)) list[atomicAdd(count, 1ull)] = (uint32_t)i;
+    }
+}
+
+// Supports of K-tuples by probing (the second k-way idea of Sec. V: look up the
+// elements of the smallest set in the others) on a set of NT = d + 1 tables,
+// for any K <= d.  A nonempty slot of the narrowest BatMap in table t at byte h
+// holds a copy of some x with pi_t(x) = ((code - 1) << s) | (h mod r_0); each
+// other set holds x in table t iff the byte at its slot for pi_t(x) carries
+// the same code.  The copy in t is counted only where all K sets hold x there
+// and t is the smallest table none of them misses (the witness), which counts
+// every element stored in all K sets once, as the scan's witness rule does;
+// elements failed in any of them come from their F lists.  One warp per routed
+// query; lanes take the narrowest BatMap's slots after a warp compaction.
+template <int K, uint32_t NT>
+__global__ void __launch_bounds__(256) k_witness_probe_k(View V, const uint32_t *__restrict__ items,
+                                                         const uint32_t *__restrict__ list,
+                                                         const unsigned long long *__restrict__ count,
+                                                         uint32_t *__restrict__ out) {
+    constexpr uint32_t CM = Fmt<NT>::CODE_MASK, CB = Fmt<NT>::CODE_BITS;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x / 32);
+    const uint64_t np = *count;
+    const uint32_t s = V.shift, r0m = (1u << s) - 1u;
+    const uint8_t *bytes = reinterpret_cast<const uint8_t *>(V.bm);
+    __shared__ uint32_t s_slots[8][512];  // per warp: the nonempty slots of 32 chunks
+    uint32_t *slots = s_slots[threadIdx.x >> 5];
+    for (uint64_t q = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) / 32; q < np; q += nwarps) {
+        const uint32_t i = list[q];
+        uint32_t it[K], lg[K];
+        uint32_t nj = 0, n_it = 0, n_lg = 0xFFFFFFFFu;  // the narrowest set (first of the narrowest)
+#pragma unroll
+        for (int j = 0; j < K; j++) {
+            it[j] = items[(uint64_t)K * i + j];
+            lg[j] = V.rlog[it[j]];
+            if (lg[j] < n_lg) {
+                n_lg = lg[j];
+                n_it = it[j];
+                nj = j;
+            }
+        }
+        // the other K - 1 sets, in order (selects keep every index static)
+        const uint8_t *ob[K - 1];
+        uint32_t orr[K - 1];
+#pragma unroll
+        for (int o = 0; o < K - 1; o++) {
+            const bool after = (uint32_t)o >= nj;
+            ob[o] = bytes + V.base[after ? it[o + 1] : it[o]];
+            orr[o] = 1u << (after ? lg[o + 1] : lg[o]);
+        }
+        const uint32_t *w0 = V.bm + (V.base[n_it] >> 2);
+        const uint32_t chunks = (NT << n_lg) / 16;  // NT r bytes of the narrowest BatMap
+        uint32_t cnt = 0;
+        const uint4 *c0 = reinterpret_cast<const uint4 *>(w0);
+        for (uint32_t base = 0; base < chunks; base += 32) {
+            const uint32_t k = base + lane;
+            const uint4 v = k < chunks ? __ldg(&c0[k]) : make_uint4(0, 0, 0, 0);
+            const uint32_t vw[4] = {v.x, v.y, v.z, v.w};
+            uint32_t n = 0;
+#pragma unroll
+            for (int j = 0; j < 16; j++) n += ((vw[j >> 2] >> (8 * (j & 3))) & CM) ? 1u : 0u;
+            uint32_t incl = n;  // inclusive prefix sum over the warp
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t o = __shfl_up_sync(0xffffffffu, incl, d);
+                if (lane >= (uint32_t)d) incl += o;
+            }
+            const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+            uint32_t pos = incl - n;
+#pragma unroll
+            for (int j = 0; j < 16; j++) {
+                const uint32_t byte = (vw[j >> 2] >> (8 * (j & 3))) & 0xFFu;
+                if (byte & CM) slots[pos++] = ((lane * 16u + (uint32_t)j) << 8) | byte;
+            }
+            __syncwarp();
+            for (uint32_t e = lane; e < total; e += 32) {
+                const uint32_t ent = slots[e], byte = ent & 0xFFu, code = byte & CM;
+                const uint32_t h = base * 16u + (ent >> 8);  // byte offset in the narrowest BatMap
+                const uint32_t t = (h >> s) % NT;
+                const uint32_t pi = ((code - 1u) << s) | (h & r0m);
+                uint32_t missed = 1u << (byte >> CB);  // tables missed by some set (each misses one)
+                bool all = true;
+#pragma unroll
+                for (int o = 0; o < K - 1; o++) {
+                    const uint32_t y = __ldg(&ob[o][slot_nt<NT>(t, pi, orr[o], s)]);
+                    all = all && (y & CM) == code;
+                    missed |= 1u << (y >> CB);
+                }
+                cnt += all && (uint32_t)(__ffs(~missed) - 1) == t ? 1u : 0u;
+            }
+            __syncwarp();
+        }
+        cnt += failed_common<K, NT>(V, it, lane);
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, d);
+        if (lane == 0) out[i] = cnt;
     }
 }
 
@@ -509,11 +637,8 @@ constexpr uint32_t GROUP = 8;
 constexpr uint32_t WG_TPB = 128;  // threads per block of k_witness_group
 static_assert(GROUP <= 8, "a unit's slot order is kept in four bits per slot of one word");
 
-// Width-skewed candidates go to the probe kernel instead of the scan: when
-// the widest of the three BatMaps is at least 2^PROBE_LOG times the
-// narrowest, the scan (which runs over the widest) costs more than visiting
-// the narrowest one's slots and probing the other two.
-constexpr uint32_t PROBE_LOG = 3;
+// Width-skewed candidates go to the probe kernel instead of the grouped scan
+// (the same PROBE_LOG rule as probe_route_k).
 __device__ __forceinline__ bool probe_route(uint32_t la, uint32_t lb, uint32_t lc) {
     return max(max(la, lb), lc) - min(min(la, lb), lc) >= PROBE_LOG;
 }
@@ -949,20 +1074,40 @@ __global__ void k_quad_candidates(const uint32_t *__restrict__ t3, uint64_t nt, 
 
 // One warp per query: k ids each, on a set of d + 1 tables.
 static void launch_witness(const wit::View &V, uint32_t d, uint32_t k, const uint32_t *d_items, uint64_t nq,
-                           uint32_t *d_support, cudaStream_t st) {
+                           uint32_t *d_support, cudaStream_t st, uint32_t skip_routed = 0) {
     using namespace wit;
     if (nq == 0) return;
     const unsigned grid = (unsigned)std::min<uint64_t>((nq + 7) / 8, 152ull * 64);
     if (d == 3) {
-        if (k == 1) k_witness<1, 4><<<grid, 256, 0, st>>>(V, d_items, nq, d_support);
-        if (k == 2) k_witness<2, 4><<<grid, 256, 0, st>>>(V, d_items, nq, d_support);
-        if (k == 3) k_witness<3, 4><<<grid, 256, 0, st>>>(V, d_items, nq, d_support);
+        if (k == 1) k_witness<1, 4><<<grid, 256, 0, st>>>(V, d_items, nq, d_support, skip_routed);
+        if (k == 2) k_witness<2, 4><<<grid, 256, 0, st>>>(V, d_items, nq, d_support, skip_routed);
+        if (k == 3) k_witness<3, 4><<<grid, 256, 0, st>>>(V, d_items, nq, d_support, skip_routed);
     } else {
-        if (k == 1) k_witness<1, 5><<<grid, 256, 0, st>>>(V, d_items, nq, d_support);
-        if (k == 2) k_witness<2, 5><<<grid, 256, 0, st>>>(V, d_items, nq, d_support);
-        if (k == 3) k_witness<3, 5><<<grid, 256, 0, st>>>(V, d_items, nq, d_support);
-        if (k == 4) k_witness<4, 5><<<grid, 256, 0, st>>>(V, d_items, nq, d_support);
+        if (k == 1) k_witness<1, 5><<<grid, 256, 0, st>>>(V, d_items, nq, d_support, skip_routed);
+        if (k == 2) k_witness<2, 5><<<grid, 256, 0, st>>>(V, d_items, nq, d_support, skip_routed);
+        if (k == 3) k_witness<3, 5><<<grid, 256, 0, st>>>(V, d_items, nq, d_support, skip_routed);
+        if (k == 4) k_witness<4, 5><<<grid, 256, 0, st>>>(V, d_items, nq, d_support, skip_routed);
     }
+    BM_CHECK_LAUNCH();
+}
+
+// Candidate supports on a 4-of-5 set with both routes: the scan kernel skips
+// the width-skewed candidates, the probe kernel takes them.  Records event 4
+// of E between the two.
+static void witness_routed5(const wit::View &V, uint32_t k, const uint32_t *d_items, uint64_t nq,
+                            const uint32_t *d_rlog, uint32_t *d_support, PhaseEvents &E, cudaStream_t st) {
+    using namespace wit;
+    if (nq == 0) return;
+    launch_witness(V, 4, k, d_items, nq, d_support, st, 1);
+    E.record(4, st);
+    DevBuf<uint32_t> plist(nq);
+    DevBuf<unsigned long long> pcount(1);
+    BM_CUDA(cudaMemsetAsync(pcount.p, 0, sizeof(unsigned long long), st));
+    if (k == 3) k_route_probe_k<3><<<grid_for(nq), 256, 0, st>>>(d_items, nq, d_rlog, plist.p, pcount.p);
+    else k_route_probe_k<4><<<grid_for(nq), 256, 0, st>>>(d_items, nq, d_rlog, plist.p, pcount.p);
+    BM_CHECK_LAUNCH();
+    if (k == 3) k_witness_probe_k<3, 5><<<152 * 16, 256, 0, st>>>(V, d_items, plist.p, pcount.p, d_support);
+    else k_witness_probe_k<4, 5><<<152 * 16, 256, 0, st>>>(V, d_items, plist.p, pcount.p, d_support);
     BM_CHECK_LAUNCH();
 }
 
@@ -1067,7 +1212,7 @@ void frequent_triples(batmap_set *S, uint32_t s, const uint32_t *d_pairs, uint64
             k_witness_probe<<<152 * 16, 256, 0, st>>>(V, cand.p, plist.p, pcount.p, sup.p);
             BM_CHECK_LAUNCH();
         } else {
-            launch_witness(V, S->d, 3, cand.p, nc, sup.p, st);  // one warp per candidate
+            witness_routed5(V, 3, cand.p, nc, S->d_rlog.p, sup.p, E, st);  // one warp per candidate or probe
         }
     }
     E.record(2, st);
@@ -1089,7 +1234,7 @@ void frequent_triples(batmap_set *S, uint32_t s, const uint32_t *d_pairs, uint64
     S->timing.compare_ms = E.ms(1, 2);
     S->timing.compact_ms = E.ms(0, 1) + E.ms(2, 3);
     S->timing.pairs_ms = E.ms(0, 3);
-    const bool split = nc && grouped;  // event 4 sits between the scan and the probe kernels
+    const bool split = nc > 0;  // event 4 sits between the scan and the probe kernels (both routes)
     S->timing.scan_ms = split ? E.ms(1, 4) : S->timing.compare_ms;
     S->timing.probe_ms = split ? E.ms(4, 2) : 0.f;
     *n_out = total;
@@ -1140,7 +1285,7 @@ void frequent_quadruples(batmap_set *S, uint32_t s, const uint32_t *d_triples, u
     if (nc) {
         const View V{reinterpret_cast<const uint32_t *>(S->d_bm.p), S->d_base.p, S->d_rlog.p, S->perm,
                      S->d_fail_off.p, S->d_fail_tid.p, S->m, S->n, S->shift};
-        launch_witness(V, 4, 4, cand.p, nc, sup.p, st);
+        witness_routed5(V, 4, cand.p, nc, S->d_rlog.p, sup.p, E, st);
     }
     E.record(2, st);
     uint64_t total = 0;
@@ -1159,6 +1304,8 @@ void frequent_quadruples(batmap_set *S, uint32_t s, const uint32_t *d_triples, u
     E.record(3, st);
     BM_CUDA(cudaStreamSynchronize(st));
     S->timing.compare_ms = E.ms(1, 2);
+    S->timing.scan_ms = nc ? E.ms(1, 4) : 0.f;  // event 4 sits between the scan and the probe kernels
+    S->timing.probe_ms = nc ? E.ms(4, 2) : 0.f;
     S->timing.compact_ms = E.ms(0, 1) + E.ms(2, 3);
     S->timing.pairs_ms = E.ms(0, 3);
     *n_out = total;

@@ -154,3 +154,36 @@ def test_rejections():
         pkg.frequent_quadruples(b3, 1, good)
     with pytest.raises(pkg.BatmapError):
         pkg.batmap_build_d(5, inst.m, off, tids, None)
+
+
+@pytest.mark.parametrize("params", [None, dict(max_loop=1, load_num=1, load_den=1)])
+def test_quadruples_probe_and_scan_routes_exact(params):
+    """Items of three densities on 4-of-5 BatMaps, so that the triple and
+    quadruple candidates split between the scan (widths within 8x) and the
+    probe route (the widest at least 8x the narrowest); s = 1 keeps every
+    candidate, and every triple and quadruple support is compared with the
+    merge oracle, also under forced failed insertions."""
+    import paper_1102_1003_gb300 as pkg
+    rng = np.random.default_rng(23)
+    m = 12_000
+    lists = [np.flatnonzero(rng.random(m) < p).astype(np.uint32) for p in [0.6] * 6 + [0.15] * 8 + [0.04] * 10]
+    inst = datagen.from_lists(lists, m, s=1)
+    pairs_ref, c3, trip_ref, c4, quad_ref = _oracle_levels(inst, 1)
+    off, tids, _ = _dev(inst, 3)
+    p = pkg.batmap_default_params(perm_seed=3, **(params or {}))
+    b2 = pkg.batmap_build(inst.m, off, tids, None, params=p)
+    _, pairs = pkg.pair_support_all(b2, 1)
+    assert np.array_equal(pairs.cpu().numpy().astype(np.uint32), pairs_ref)
+    b4 = pkg.batmap_build_d(D, inst.m, off, tids, None, params=p)
+    lg = np.log2(pkg.batmap_export_layout(b4)["range"].astype(np.float64)).astype(np.int64)
+    for cand in (c3, c4):
+        spread = lg[cand].max(axis=1) - lg[cand].min(axis=1)
+        assert (spread >= 3).sum() > 100 and (spread < 3).sum() > 100
+    if params:
+        assert b4.info["n_failed"] > 0
+    n3, trip, n3c = pkg.frequent_triples(b4, 1, pairs)
+    assert n3c == c3.shape[0] and n3 == trip_ref.shape[0]
+    assert np.array_equal(trip.cpu().numpy().astype(np.uint32), trip_ref)
+    n4, quad, n4c = pkg.frequent_quadruples(b4, 1, trip)
+    assert n4c == c4.shape[0] and n4 == quad_ref.shape[0]
+    assert np.array_equal(quad.cpu().numpy().astype(np.uint32), quad_ref)
