@@ -459,7 +459,12 @@ __device__ __forceinline__ uint32_t failed_common(const View &V, const uint32_t 
 // slots and probing the others (a same-box sweep of the frequent-triples
 // step put the best threshold at 8x).
 constexpr uint32_t PROBE_LOG = 3;
-template <int K>
+// On 4-of-5 sets the scan alternative is the one-warp-per-candidate kernel, so
+// the probe pays from a width ratio of 2 on (same-box sweep of the frequent
+// quadruples step on the Zipf triples workload: 2x 106.7 ms, 4x 110.5 ms,
+// 8x 144.8 ms).
+constexpr uint32_t PROBE_LOG5 = 1;
+template <int K, uint32_t NT>
 __device__ __forceinline__ bool probe_route_k(const uint32_t (&lg)[K]) {
     uint32_t lo = lg[0], hi = lg[0];
 #pragma unroll
@@ -467,7 +472,7 @@ __device__ __forceinline__ bool probe_route_k(const uint32_t (&lg)[K]) {
         lo = min(lo, lg[j]);
         hi = max(hi, lg[j]);
     }
-    return hi - lo >= PROBE_LOG;
+    return hi - lo >= (NT == 5 ? PROBE_LOG5 : PROBE_LOG);
 }
 
 // skip_routed: leave the width-skewed queries (probe_route_k) to
@@ -489,7 +494,7 @@ __global__ void __launch_bounds__(256) k_witness(View V, const uint32_t *__restr
             wb[j] = V.base[it[j]] >> 2;
             wmax = max(wmax, NT << e[j]);
         }
-        if (skip_routed && probe_route_k<K>(lg)) continue;
+        if (skip_routed && probe_route_k<K, NT>(lg)) continue;
         const uint32_t tshift = V.shift - 2;  // words per table block = r_0 / 4
         uint32_t cnt = 0;
         for (uint32_t w = lane; w < wmax; w += 32) {
@@ -511,14 +516,14 @@ __global__ void __launch_bounds__(256) k_witness(View V, const uint32_t *__restr
 }
 
 // Indices of the queries of K items routed to the probe kernel (any order).
-template <int K>
+template <int K, uint32_t NT>
 __global__ void k_route_probe_k(const uint32_t *__restrict__ items, uint64_t nq, const uint32_t *__restrict__ rlog,
                                 uint32_t *__restrict__ list, unsigned long long *__restrict__ count) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nq; i += (uint64_t)gridDim.x * blockDim.x) {
         uint32_t lg[K];
 #pragma unroll
         for (int j = 0; j < K; j++) lg[j] = rlog[items[K * i + j]];
-        if (probe_route_k<K>(lg)) list[atomicAdd(count, 1ull)] = (uint32_t)i;
+        if (probe_route_k<K, NT>(lg)) list[atomicAdd(count, 1ull)] = (uint32_t)i;
     }
 }
 
@@ -1103,8 +1108,8 @@ static void witness_routed5(const wit::View &V, uint32_t k, const uint32_t *d_it
     DevBuf<uint32_t> plist(nq);
     DevBuf<unsigned long long> pcount(1);
     BM_CUDA(cudaMemsetAsync(pcount.p, 0, sizeof(unsigned long long), st));
-    if (k == 3) k_route_probe_k<3><<<grid_for(nq), 256, 0, st>>>(d_items, nq, d_rlog, plist.p, pcount.p);
-    else k_route_probe_k<4><<<grid_for(nq), 256, 0, st>>>(d_items, nq, d_rlog, plist.p, pcount.p);
+    if (k == 3) k_route_probe_k<3, 5><<<grid_for(nq), 256, 0, st>>>(d_items, nq, d_rlog, plist.p, pcount.p);
+    else k_route_probe_k<4, 5><<<grid_for(nq), 256, 0, st>>>(d_items, nq, d_rlog, plist.p, pcount.p);
     BM_CHECK_LAUNCH();
     if (k == 3) k_witness_probe_k<3, 5><<<152 * 16, 256, 0, st>>>(V, d_items, plist.p, pcount.p, d_support);
     else k_witness_probe_k<4, 5><<<152 * 16, 256, 0, st>>>(V, d_items, plist.p, pcount.p, d_support);

@@ -159,8 +159,8 @@ def test_rejections():
 @pytest.mark.parametrize("params", [None, dict(max_loop=1, load_num=1, load_den=1)])
 def test_quadruples_probe_and_scan_routes_exact(params):
     """Items of three densities on 4-of-5 BatMaps, so that the triple and
-    quadruple candidates split between the scan (widths within 8x) and the
-    probe route (the widest at least 8x the narrowest); s = 1 keeps every
+    quadruple candidates split between the scan (equal widths) and the probe
+    route (the widest at least 2x the narrowest); s = 1 keeps every
     candidate, and every triple and quadruple support is compared with the
     merge oracle, also under forced failed insertions."""
     import paper_1102_1003_gb300 as pkg
@@ -178,7 +178,7 @@ def test_quadruples_probe_and_scan_routes_exact(params):
     lg = np.log2(pkg.batmap_export_layout(b4)["range"].astype(np.float64)).astype(np.int64)
     for cand in (c3, c4):
         spread = lg[cand].max(axis=1) - lg[cand].min(axis=1)
-        assert (spread >= 3).sum() > 100 and (spread < 3).sum() > 100
+        assert (spread >= 1).sum() > 100 and (spread == 0).sum() >= 15
     if params:
         assert b4.info["n_failed"] > 0
     n3, trip, n3c = pkg.frequent_triples(b4, 1, pairs)
