@@ -237,11 +237,15 @@ batmap_status itemset_support(batmap_set *set, uint32_t k, uint64_t n_q, const u
  *   d_out   : device uint32[4 * cap], (a, b, c, support), lexicographic.
  *   n_out   : host, number of frequent triples (all of them, even > cap).
  *   n_candidates : host, may be NULL; number of candidates counted.
- * The set may be built with d = 3 (grouped witness kernel) or d = 4 (one
- * warp per candidate).  Synchronises `stream`.  Timing: compare_ms = the
- * support kernel, compact_ms = candidate generation + compaction, pairs_ms =
- * the call.  Errors: BATMAP_ERR_ARG, BATMAP_ERR_CAPACITY (cap < *n_out; the
- * first cap triples are written).
+ * The set may be built with d = 3 or d = 4.  Candidates whose widest BatMap
+ * is at least 8x (d = 3) or 2x (d = 4) the narrowest are counted by probing
+ * the narrowest set's slots in the others (Sec. V: look up the elements of
+ * the smallest set); the rest by the witness scan (grouped by pair for d = 3,
+ * one warp per candidate for d = 4).  Both count the same elements.
+ * Synchronises `stream`.  Timing: compare_ms = the support kernels (scan_ms
+ * the scan, probe_ms the probe), compact_ms = candidate generation +
+ * compaction, pairs_ms = the call.  Errors: BATMAP_ERR_ARG,
+ * BATMAP_ERR_CAPACITY (cap < *n_out; the first cap triples are written).
  */
 batmap_status frequent_triples(batmap_set *set, uint32_t s, const uint32_t *d_pairs, uint64_t n_pairs,
                                uint32_t *d_out, uint64_t cap, uint64_t *n_out, uint64_t *n_candidates,
@@ -260,9 +264,10 @@ batmap_status frequent_triples(batmap_set *set, uint32_t s, const uint32_t *d_pa
  *   d_out     : device uint32[5 * cap], (a, b, c, d, support), lexicographic.
  *   n_out     : host, number of frequent quadruples (all of them, even > cap).
  *   n_candidates : host, may be NULL; number of candidates counted.
- * Needs a set built with d = 4.  Synchronises `stream`; timing as
- * frequent_triples.  Errors: BATMAP_ERR_ARG, BATMAP_ERR_CAPACITY (the first
- * cap quadruples are written).
+ * Needs a set built with d = 4; candidates are routed between the probe and
+ * the scan as in frequent_triples on a d = 4 set.  Synchronises `stream`;
+ * timing as frequent_triples.  Errors: BATMAP_ERR_ARG, BATMAP_ERR_CAPACITY
+ * (the first cap quadruples are written).
  */
 batmap_status frequent_quadruples(batmap_set *set, uint32_t s, const uint32_t *d_triples, uint64_t n_triples,
                                   uint32_t *d_out, uint64_t cap, uint64_t *n_out, uint64_t *n_candidates,
@@ -353,10 +358,10 @@ typedef struct batmap_timing {
     float compare_ms;   /* the all-pairs compare: scan and probe kernels        */
     float compact_ms;   /* failure correction + threshold compaction            */
     float pairs_ms;     /* whole pair_support_all                               */
-    float scan_ms;      /* frequent_triples: the witness scan kernel;
+    float scan_ms;      /* frequent_triples / _quadruples: the witness scan;
                            pair_support_all: the cyclic-scan compare kernels    */
-    float probe_ms;     /* frequent_triples and pair_support_all: the probe
-                           kernel of width-skewed tuples                        */
+    float probe_ms;     /* frequent_triples / _quadruples and pair_support_all:
+                           the probe kernel of width-skewed tuples              */
 } batmap_timing;
 
 /* Copy the phase durations of the set's most recent calls into *t. */
