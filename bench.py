@@ -382,11 +382,11 @@ def plain_leg(inst, dev, steps, warmup, peaks, peak_kind, workload, sampler=None
             "kernel": "k_pair_probe", "ms": 1e3 * probe_s, "routed_word_pairs": wp_probe,
             "routed_share": wp_probe / wp, "words_read": info["probe_words"],
             "scan_equivalent_frac": OPS_PER_WORD_PAIR * wp_probe / probe_s / 1e12 / alu_peak,
-            "definition": "pairs whose BatMap widths differ by 2^probe_log or more (default 32x) are counted "
-                          "by probing the narrower BatMap's nonempty slots; routed_word_pairs is the scan's "
-                          "work for them (max(|B_i|,|B_j|)/4 per pair), words_read the probe's "
-                          "(min(|B_i|,|B_j|)/4 per pair); scan_equivalent_frac = 4 x routed_word_pairs / "
-                          "probe time / lane-op peak",
+            "definition": "pairs whose BatMap widths differ by 2^probe_log or more (default 4x) are eligible; "
+                          "per width class the scheduler's cost model picks the rows it counts by probing the "
+                          "narrower BatMap's nonempty slots; routed_word_pairs is the scan's work for them "
+                          "(max(|B_i|,|B_j|)/4 per pair), words_read the probe's (min(|B_i|,|B_j|)/4 per "
+                          "pair); scan_equivalent_frac = 4 x routed_word_pairs / probe time / lane-op peak",
             "traffic": _traffic(workload, "k_pair_probe"),
         }
     return rec, off, tids, n_out
